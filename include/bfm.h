@@ -1,0 +1,181 @@
+/*
+ * bfm.h -- C ABI of the GB300 BFAST Monitor library (libbfm.so).
+ *
+ * BFAST Monitor (von Mehren et al., "Massively-Parallel Break Detection for
+ * Satellite Data", 2018) fits, for every pixel of an image time series, the
+ * season-trend model of Section 2.1 (Eq. 1-2) by least squares on a stable
+ * history period (Eq. 5-6), then tests the residual MOSUM process of the
+ * monitoring period (Eq. 3) against the boundary lambda*sqrt(log+(t/n))
+ * (Eq. 4); Algorithm 1 lists the steps for one series, Algorithm 2 the
+ * many-series form this library implements on the GPU.
+ *
+ * Conventions common to all calls
+ *  - No exceptions and no aborts cross this ABI.  Every call returns a
+ *    bfm_status; on failure bfm_last_error() gives a message (per thread).
+ *  - Device pointers are CUDA device addresses on the current device; the
+ *    caller owns them and keeps them alive until the work on `stream` ends.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device calls only enqueue work and return; nothing
+ *    synchronises unless stated.
+ *  - Y is time-major: Y[t*m + p] is date t of pixel p (the matrix Y of
+ *    Section 3, Eq. 7).  BFM_F32: float, NaN marks a missing observation.
+ *    BFM_I16: int16 (e.g. NDVI*1e4), -32768 marks a missing observation; the
+ *    stored integers are the series values (outputs are in those units).
+ *  - mask_bits (nullable) adds an explicit validity mask [N][ceil(m/32)]
+ *    uint32 words, bit (p % 32) of word p/32 of row t, 1 = valid; it is
+ *    ANDed with the missing marker.
+ *  - Missing data (a reading; the paper assumes complete series, Section 3):
+ *    each pixel keeps its valid observations in date order; history size
+ *    n_p counts valid observations among the first n_hist dates; MOSUM
+ *    positions, n and h count valid observations; regressors use the actual
+ *    date values (Section 4.3).  For complete series this is exactly
+ *    Algorithm 1 with h terms per window (Eq. 3, Algorithm 3).
+ */
+#ifndef BFM_H
+#define BFM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BFM_OK = 0,
+    BFM_EINVAL = 1,      /* an argument is out of range (message says which) */
+    BFM_ENOMEM = 2,      /* a host or device allocation failed */
+    BFM_ECUDA = 3,       /* a CUDA runtime/driver call failed */
+    BFM_ETIMEOUT = 4,    /* a bounded wait gave up (device error word set) */
+    BFM_EBUSY = 5,       /* admission refused: over the memory budget */
+    BFM_EUNSUPPORTED = 6 /* valid request this build cannot run (e.g. N too long) */
+} bfm_status;
+
+typedef enum { BFM_F32 = 0, BFM_I16 = 1 } bfm_dtype;
+
+/* Per-pixel status codes written to the `status` output (not errors). */
+enum {
+    BFM_PX_OK = 0,
+    BFM_PX_INSUFFICIENT_HISTORY = 1, /* n_p <= K: no fit; beta, sigma, mean NaN */
+    BFM_PX_SINGULAR = 2,             /* rank test failed (see bfm_monitor); NaN outputs */
+    BFM_PX_DEGENERATE = 3,           /* sigma-hat <= 1e-6 max|y_hist|: MO = 0, mean 0 */
+    BFM_PX_NO_MONITOR = 4,           /* no valid monitoring observation: mean NaN */
+    BFM_PX_TIMEOUT = 255             /* the tile's load wait gave up (device error) */
+};
+
+/* Algorithm variants for bfm_monitor_ex (BFM_ALGO_AUTO picks by dtype). */
+typedef enum {
+    BFM_ALGO_AUTO = 0,
+    BFM_ALGO_SIMT = 1, /* FP32 CUDA-core path ("plain form") */
+    BFM_ALGO_MMA = 2   /* tensor-core normal equations ("precision form") */
+} bfm_algo;
+
+typedef struct bfm_design_s *bfm_design_t;
+
+/* Library version string, e.g. "bfm 0.1.0 sm_103a". */
+const char *bfm_version(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *bfm_last_error(void);
+
+/*
+ * bfm_design_create -- season-trend design for one set of acquisition dates
+ * (Algorithm 1, step 1; regressors of Eq. 2).
+ *   dates  host, N doubles, strictly increasing date values in a unit in
+ *          which f dates make one seasonal period (t = index for regular
+ *          series; day numbers with f = 365 for irregular ones, Section 4.3).
+ *   N      number of dates, 2 <= N <= bfm_max_dates().
+ *   k_harm number of harmonic terms k, 1 <= k <= 3 (K = 2 + 2k regressors).
+ *   f      season length (frequency), f > 0.
+ *   out    receives a handle.  Identical (dates, k, f) share one cached
+ *          handle (reference counted).  The library owns the handle and its
+ *          device tables (allocated on the current device).
+ * Internally the trend column is centred and scaled, t' = (t - c)/s with c,
+ * s the midpoint and half-range of the dates; results are mapped back to the
+ * raw parameterisation of Eq. 2.
+ * Errors: BFM_EINVAL (bad argument), BFM_ENOMEM, BFM_ECUDA.
+ */
+bfm_status bfm_design_create(const double *dates, int N, int k_harm, double f, bfm_design_t *out);
+
+/* Drop one reference; the design is freed with its last reference.  Device
+ * work that uses it must have finished. */
+bfm_status bfm_design_destroy(bfm_design_t d);
+
+/* K = 2 + 2k of the design (0 for a NULL handle). */
+int bfm_design_K(bfm_design_t d);
+
+/* N of the design (0 for a NULL handle). */
+int bfm_design_N(bfm_design_t d);
+
+/* Longest date set this build processes in one pass (tile held on chip). */
+int bfm_max_dates(void);
+
+/*
+ * bfm_monitor -- the per-pixel hot path for m pixels on `stream`.
+ * For each pixel p (Algorithm 1 steps 2-12 with the missing-data reading):
+ *   beta    OLS fit on the valid history observations (Eq. 5-6);
+ *   sigma   sqrt(sum of squared history residuals / (n_p - K)) (Alg. 1 step 5);
+ *   MO_j    sum of the h_p residuals y - x'beta ending at valid position j,
+ *           divided by sigma*sqrt(n_p), for j = n_p+1 .. N_p (Eq. 3), with
+ *           h_p = clamp(floor(h_frac * n_p), 1, n_p);
+ *   break   original date index of the first j with |MO_j| >
+ *           lambda*sqrt(log+(j/n_p)) (Eq. 4, strict), else -1;
+ *   mean    mean of MO_j over the monitoring positions.
+ * Arguments:
+ *   d          design (its N is the number of rows of Y).
+ *   Y          device, [N][m] of `dtype` (16-byte aligned base and m a
+ *              multiple of 4 (f32) / 8 (i16) take the TMA tile loader; other
+ *              layouts take a plain-load loader with the same results).
+ *   mask_bits  device, nullable, [N][ceil(m/32)] uint32 (see above).
+ *   m          number of pixels, m >= 0 (m = 0 enqueues nothing).
+ *   n_hist     history dates, 1 <= n_hist < N (Algorithm 1 Require list).
+ *   h_frac     bandwidth as a fraction of n_p, 0 < h_frac <= 1.
+ *   lambda     critical value, lambda > 0 (depends on alpha, h and N/n).
+ * Outputs (device, caller-owned, each written for every pixel):
+ *   break_idx  int32 [m]; mean_mosum float [m]; sigma float [m];
+ *   beta       float [K][m] (coefficient i of pixel p at beta[i*m + p], Eq. 2
+ *              order: intercept, slope, then sin/cos pairs per harmonic);
+ *   status     uint8 [m] (BFM_PX_*).
+ * Rank test: with the trend column (t-c)/s, the pixel is SINGULAR when some
+ * Cholesky pivot of its history Gram matrix, relative to the matching
+ * diagonal entry, is below 1e-5.
+ * Arithmetic: float storage, float arithmetic, one step of iterative
+ * refinement of the least-squares solution.
+ * Errors: BFM_EINVAL, BFM_EUNSUPPORTED (N > bfm_max_dates()), BFM_ECUDA.
+ */
+bfm_status bfm_monitor(bfm_design_t d, const void *Y, int dtype, const uint32_t *mask_bits, int64_t m,
+                       int n_hist, double h_frac, double lambda, int32_t *break_idx, float *mean_mosum,
+                       float *sigma, float *beta, uint8_t *status, void *stream);
+
+/* As bfm_monitor with an explicit algorithm (bfm_algo).  BFM_ALGO_MMA needs
+ * dtype BFM_I16. */
+bfm_status bfm_monitor_ex(bfm_design_t d, const void *Y, int dtype, const uint32_t *mask_bits, int64_t m,
+                          int n_hist, double h_frac, double lambda, int32_t *break_idx, float *mean_mosum,
+                          float *sigma, float *beta, uint8_t *status, int algo, void *stream);
+
+/*
+ * bfm_monitor_host -- the same computation on HOST buffers (Algorithm 2,
+ * steps 2 and 15: transfer Y in, breaks out).  Y_host [N][m] and mask_host
+ * (nullable) are read, the five outputs are written to host memory, with the
+ * pixel range cut into chunks whose host->device copy, kernel and
+ * device->host copy overlap on internal streams.  Page-locked host memory is
+ * needed for the copies to overlap.  `workspace` is a device buffer of at
+ * least bfm_monitor_host_workspace(d, dtype, chunk_px, with_mask) bytes,
+ * owned by the caller; chunk_px > 0 is the pixels per chunk.  Returns once
+ * the work is enqueued on `stream`; the outputs are ready when `stream` is.
+ */
+size_t bfm_monitor_host_workspace(bfm_design_t d, int dtype, int64_t chunk_px, int with_mask);
+bfm_status bfm_monitor_host(bfm_design_t d, const void *Y_host, int dtype, const uint32_t *mask_host,
+                            int64_t m, int n_hist, double h_frac, double lambda, int32_t *break_idx,
+                            float *mean_mosum, float *sigma, float *beta, uint8_t *status, void *workspace,
+                            size_t workspace_bytes, int64_t chunk_px, void *stream);
+
+/* Reads and clears the library's device error word (bit 0: a tile load wait
+ * gave up).  Synchronises `stream`. */
+bfm_status bfm_device_errors(void *stream, uint32_t *bits);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BFM_H */
