@@ -1,0 +1,307 @@
+#!/usr/bin/env python3
+"""Benchmark: BFAST Monitor pixels/s on the full synthetic scene.
+
+Workload (the default): 8,388,608 pixels (4096 x 2048) x 414 irregular dates,
+history = first 228 dates, 3 harmonics + intercept + trend (K = 8), f = 23,
+h = 0.25 n, lambda for alpha = 0.05; float32 storage with NaN for ~60 %
+Markov cloud gaps; 10 % of pixels with a level shift.  One step = one
+bfm_monitor call over the whole scene (every step of the per-pixel path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--form f32|i16] [--no-e2e] [--no-cpu-baseline]
+
+Prints ONE JSON line (rank 0).  Under torchrun (N > 1) every rank processes
+its own full scene (weak scaling, no collective on the data path); value is
+all ranks' pixels / the slowest rank's time.
+
+``--impl reference``: the FP64 oracle (plain C, all host cores) on a bounded
+sample of the same scene per step -- a deliberately slow baseline, not the
+target.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BFAST-monitor pixels/s at 8.4M px x 414 dates; p50/p99 tile latency"
+WORKLOAD = "c2: full scene 8,388,608 px x 414 dates, n_hist=228, K=8, f=23, h=0.25, plain float32"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(w_np_Y, dates, k, f, n_hist, h_frac, lam, budget_s: float):
+    """Time the oracle on a bounded sample (columns of the same scene)."""
+    import oracle
+    m_all = w_np_Y.shape[1]
+    cal = min(1024, m_all)
+    t0 = time.perf_counter()
+    oracle.monitor(dates, w_np_Y[:, :cal], k=k, f=f, n_hist=n_hist, h_frac=h_frac, lam=lam)
+    rate = cal / (time.perf_counter() - t0)
+    n = int(min(m_all, max(cal, rate * budget_s)))
+    t0 = time.perf_counter()
+    oracle.monitor(dates, w_np_Y[:, :n], k=k, f=f, n_hist=n_hist, h_frac=h_frac, lam=lam)
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    import torch
+    w = synth.workload_torch("c2", device="cpu", m=1 << 18)
+    Y = w["Y"].numpy()
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    # size each step so the whole run takes about two minutes
+    t0 = time.perf_counter()
+    oracle.monitor(w["dates"], Y[:, :512], k=3, f=23.0, n_hist=228, h_frac=0.25, lam=w["lam"])
+    rate = 512 / (time.perf_counter() - t0)
+    per_step = int(max(256, min(Y.shape[1], rate * 100.0 / max(1, args.steps + args.warmup))))
+    times = []
+    for s in range(args.warmup + args.steps):
+        c0 = (s * per_step) % (Y.shape[1] - per_step + 1)
+        sub = Y[:, c0:c0 + per_step]
+        t0 = time.perf_counter()
+        oracle.monitor(w["dates"], sub, k=3, f=23.0, n_hist=228, h_frac=0.25, lam=w["lam"])
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    val = per_step * len(times) / tot
+    sample = f"{per_step} pixel columns of the c2 scene per step (all 414 dates), oracle in FP64"
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "pixels/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_px_per_step": per_step},
+            "cpu_baseline": {"value": val, "unit": "pixels/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": "pixels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1807_01751_gb300 as bfm
+    import synth
+    bfm.load()
+
+    name = "c2"
+    w = synth.workload_torch(name, device=dev, dtype="f32")
+    m, N, n_hist, K = w["m"], w["N"], w["n_hist"], 8
+    Y = w["Y"]
+    form = args.form
+    if form == "i16":
+        Y = torch.where(torch.isnan(Y), torch.full_like(Y, -32768.0),
+                        torch.clamp(torch.round(Y * 1e4), -32767, 32767)).to(torch.int16)
+    dtype_code = bfm.BFM_F32 if form == "f32" else bfm.BFM_I16
+    algo = bfm.BFM_ALGO_SIMT
+    design = bfm.Design(w["dates"], 3, 23.0)
+    out = bfm.empty_outputs(K, m, dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        bfm.bfm_monitor_ex(design, Y, dtype_code, None, m, n_hist, w["h_frac"], w["lam"], out["break_idx"],
+                           out["mean_mosum"], out["sigma"], out["beta"], out["status"], algo, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if bfm.bfm_device_errors(stream) != 0:
+        raise RuntimeError("device error word set during warm-up")
+    clocks = Clocks(local)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.2)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record(stream)
+    for i in range(args.steps):
+        step()
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = ws * m * args.steps / (total_ms / 1e3)
+    ms_step = total_ms / args.steps
+    elt = 4 if form == "f32" else 2
+    alg_bytes = N * m * elt + m * (4 + 4 + 4 + 4 * K + 1)
+    hbm, peak_kind = _peaks()
+    achieved = alg_bytes / (statistics.mean(per) / 1e3) / 1e9
+
+    # ---- end to end through the host-buffer entry point ------------------------------
+    e2e = None
+    if not args.no_e2e:
+        Yh = torch.empty(Y.shape, dtype=Y.dtype, pin_memory=True)
+        Yh.copy_(Y)
+        oh = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()}
+        chunk = 1 << 20
+        wsb = bfm.bfm_monitor_host_workspace(design, dtype_code, chunk, False)
+        wbuf = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        del Y
+        torch.cuda.empty_cache()
+
+        def hstep():
+            bfm.bfm_monitor_host(design, Yh, dtype_code, None, m, n_hist, w["h_frac"], w["lam"], oh["break_idx"],
+                                 oh["mean_mosum"], oh["sigma"], oh["beta"], oh["status"], wbuf, wsb, chunk, stream)
+
+        hstep()
+        torch.cuda.synchronize()
+        e_steps = max(2, min(args.steps, 10))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e_steps):
+            hstep()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1) / e_steps
+        if ws > 1:
+            t = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": ws * m / (e_ms / 1e3), "unit": "pixels/s", "h2d_bytes_per_step": N * m * elt,
+               "d2h_bytes_per_step": m * (4 + 4 + 4 + 4 * K + 1), "ms_per_step": e_ms,
+               "api": "bfm_monitor_host (pinned host Y and outputs, 1 Mi-pixel chunks)"}
+        Ynp = Yh[:, :1 << 17].numpy().copy()
+    else:
+        Ynp = Y[:, :1 << 17].cpu().numpy()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, n, dt = cpu_oracle_rate(Ynp, w["dates"], 3, 23.0, n_hist, w["h_frac"], w["lam"], budget_s=15.0)
+        cpu = {"value": rate, "unit": "pixels/s", "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count())),
+               "kind": "oracle", "sample": f"first {n} pixels of the same scene, all {N} dates, FP64 oracle ({dt:.1f} s)"}
+
+    srt = sorted(per)
+    line = {
+        "metric": METRIC, "value": value, "unit": "pixels/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if form == "f32" else "i16", "data": "synthetic",
+        "config": {"workload": WORKLOAD if form == "f32" else WORKLOAD.replace("plain float32", "int16 storage"),
+                   "pixels": m, "dates": N, "n_hist": n_hist, "K": K, "form": form,
+                   "algo": "simt", "l2": "inputs larger than L2 (Y is %.1f GB per step)" % (N * m * elt / 1e9),
+                   "parallelism": f"{ws} independent scene(s), one per GPU"},
+        "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)],
+                       "unit": "one full-scene call"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+                     "algorithmic_bytes_per_launch": alg_bytes},
+        "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": args.steps,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="f32", choices=["f32", "i16"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

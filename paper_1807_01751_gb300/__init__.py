@@ -1,0 +1,217 @@
+"""GB300-native BFAST Monitor: Python binding of libbfm (include/bfm.h).
+
+Argument marshalling only.  Every step of the per-pixel path (tile staging,
+masking, normal equations, solve, residuals, MOSUM, detection) runs in the
+library's CUDA kernels.  PyTorch provides device memory and streams.  There
+is no CPU path: without the compiled library every call raises.
+
+    import torch, paper_1807_01751_gb300 as bfm
+    d = bfm.Design(dates, k=3, f=23.0)                  # bfm_design_create
+    out = bfm.monitor(d, Y, n_hist=228, h_frac=0.25, lam=1.69)   # bfm_monitor
+    out["break_idx"], out["mean_mosum"], out["sigma"], out["beta"], out["status"]
+
+The C names are exported too (``bfm_design_create``, ``bfm_monitor``,
+``bfm_monitor_ex``, ``bfm_monitor_host``, ...), taking raw pointers/ints.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import _build
+
+BFM_F32, BFM_I16 = 0, 1
+BFM_ALGO_AUTO, BFM_ALGO_SIMT, BFM_ALGO_MMA = 0, 1, 2
+STATUS_NAMES = {0: "OK", 1: "INSUFFICIENT_HISTORY", 2: "SINGULAR", 3: "DEGENERATE", 4: "NO_MONITOR",
+                255: "TIMEOUT"}
+ERRORS = {1: "BFM_EINVAL", 2: "BFM_ENOMEM", 3: "BFM_ECUDA", 4: "BFM_ETIMEOUT", 5: "BFM_EBUSY",
+          6: "BFM_EUNSUPPORTED"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class BfmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.SO
+
+
+def load(build_if_missing: bool = True):
+    """Load libbfm.so (compiling it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        so = _build.build() if build_if_missing else _build.SO
+        if not os.path.exists(so):
+            raise RuntimeError(f"libbfm.so not found at {so}; run __graft_entry__.build()")
+        lib = ctypes.CDLL(so)
+        vp, i32, i64, dbl, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+        lib.bfm_version.restype = ctypes.c_char_p
+        lib.bfm_last_error.restype = ctypes.c_char_p
+        lib.bfm_max_dates.restype = i32
+        lib.bfm_design_create.argtypes = [vp, i32, i32, dbl, ctypes.POINTER(vp)]
+        lib.bfm_design_create.restype = i32
+        lib.bfm_design_destroy.argtypes = [vp]
+        lib.bfm_design_destroy.restype = i32
+        lib.bfm_design_K.argtypes = [vp]
+        lib.bfm_design_K.restype = i32
+        lib.bfm_design_N.argtypes = [vp]
+        lib.bfm_design_N.restype = i32
+        mon = [vp, vp, i32, vp, i64, i32, dbl, dbl, vp, vp, vp, vp, vp]
+        lib.bfm_monitor.argtypes = mon + [vp]
+        lib.bfm_monitor.restype = i32
+        lib.bfm_monitor_ex.argtypes = mon + [i32, vp]
+        lib.bfm_monitor_ex.restype = i32
+        lib.bfm_monitor_host_workspace.argtypes = [vp, i32, i64, i32]
+        lib.bfm_monitor_host_workspace.restype = sz
+        lib.bfm_monitor_host.argtypes = mon + [vp, sz, i64, vp]
+        lib.bfm_monitor_host.restype = i32
+        lib.bfm_device_errors.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
+        lib.bfm_device_errors.restype = i32
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise BfmError(rc, load().bfm_last_error().decode())
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x)}")
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---- C names -----------------------------------------------------------------
+
+def bfm_version() -> str:
+    return load().bfm_version().decode()
+
+
+def bfm_last_error() -> str:
+    return load().bfm_last_error().decode()
+
+
+def bfm_max_dates() -> int:
+    return load().bfm_max_dates()
+
+
+def bfm_design_create(dates, k_harm: int, f: float) -> int:
+    import numpy as np
+    d = np.ascontiguousarray(dates, dtype=np.float64)
+    h = ctypes.c_void_p()
+    _check(load().bfm_design_create(d.ctypes.data, int(d.size), int(k_harm), float(f), ctypes.byref(h)))
+    return h.value
+
+
+def bfm_design_destroy(handle: int):
+    _check(load().bfm_design_destroy(handle))
+
+
+def bfm_design_K(handle: int) -> int:
+    return load().bfm_design_K(handle)
+
+
+def bfm_monitor(design, Y, dtype, mask_bits, m, n_hist, h_frac, lam, break_idx, mean_mosum, sigma, beta,
+                status, stream=None):
+    _check(load().bfm_monitor(int(design), _ptr(Y), int(dtype), _ptr(mask_bits), int(m), int(n_hist),
+                              float(h_frac), float(lam), _ptr(break_idx), _ptr(mean_mosum), _ptr(sigma),
+                              _ptr(beta), _ptr(status), _stream(stream)))
+
+
+def bfm_monitor_ex(design, Y, dtype, mask_bits, m, n_hist, h_frac, lam, break_idx, mean_mosum, sigma, beta,
+                   status, algo, stream=None):
+    _check(load().bfm_monitor_ex(int(design), _ptr(Y), int(dtype), _ptr(mask_bits), int(m), int(n_hist),
+                                 float(h_frac), float(lam), _ptr(break_idx), _ptr(mean_mosum), _ptr(sigma),
+                                 _ptr(beta), _ptr(status), int(algo), _stream(stream)))
+
+
+def bfm_monitor_host_workspace(design, dtype: int, chunk_px: int, with_mask: bool) -> int:
+    return load().bfm_monitor_host_workspace(int(design), int(dtype), int(chunk_px), int(bool(with_mask)))
+
+
+def bfm_monitor_host(design, Y_host, dtype, mask_host, m, n_hist, h_frac, lam, break_idx, mean_mosum, sigma,
+                     beta, status, workspace, workspace_bytes, chunk_px, stream=None):
+    _check(load().bfm_monitor_host(int(design), _ptr(Y_host), int(dtype), _ptr(mask_host), int(m), int(n_hist),
+                                   float(h_frac), float(lam), _ptr(break_idx), _ptr(mean_mosum), _ptr(sigma),
+                                   _ptr(beta), _ptr(status), _ptr(workspace), int(workspace_bytes),
+                                   int(chunk_px), _stream(stream)))
+
+
+def bfm_device_errors(stream=None) -> int:
+    v = ctypes.c_uint32(0)
+    _check(load().bfm_device_errors(_stream(stream), ctypes.byref(v)))
+    return v.value
+
+
+# ---- convenience layer ----------------------------------------------------------
+
+class Design:
+    """Owning wrapper of a bfm_design_t (Algorithm 1, step 1)."""
+
+    def __init__(self, dates, k: int, f: float):
+        self.handle = bfm_design_create(dates, k, f)
+        self.k = int(k)
+        self.K = 2 + 2 * self.k
+        self.N = len(dates)
+        self.f = float(f)
+
+    def close(self):
+        if self.handle:
+            bfm_design_destroy(self.handle)
+            self.handle = 0
+
+    def __int__(self):
+        return int(self.handle)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def empty_outputs(K: int, m: int, device="cuda"):
+    import torch
+    return dict(break_idx=torch.empty(m, dtype=torch.int32, device=device),
+                mean_mosum=torch.empty(m, dtype=torch.float32, device=device),
+                sigma=torch.empty(m, dtype=torch.float32, device=device),
+                beta=torch.empty((K, m), dtype=torch.float32, device=device),
+                status=torch.empty(m, dtype=torch.uint8, device=device))
+
+
+def monitor(design: Design, Y, *, n_hist: int, h_frac: float, lam: float, mask_bits=None, out=None,
+            algo: int = BFM_ALGO_AUTO, stream=None):
+    """Run bfm_monitor_ex on a device tensor Y [N][m] (float32 or int16)."""
+    import torch
+    assert Y.is_cuda and Y.dim() == 2 and Y.is_contiguous()
+    dtype = {torch.float32: BFM_F32, torch.int16: BFM_I16}[Y.dtype]
+    m = Y.shape[1]
+    if out is None:
+        out = empty_outputs(design.K, m, Y.device)
+    bfm_monitor_ex(design, Y, dtype, mask_bits, m, n_hist, h_frac, lam, out["break_idx"], out["mean_mosum"],
+                   out["sigma"], out["beta"], out["status"], algo, stream)
+    return out

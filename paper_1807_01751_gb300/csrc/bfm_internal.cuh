@@ -1,0 +1,105 @@
+// Internal declarations of libbfm (not part of the public ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bfm.h"
+
+namespace bfm {
+
+// ---------------------------------------------------------------------------
+// Per-date basis row.
+//
+// The normal equations of Eq. 6 need, per pixel, G = sum_t m_t x_t x_t' with
+// x_t the Eq. 2 regressors.  Products of harmonics reduce to single harmonics
+// (sin a sin b = [cos(a-b) - cos(a+b)]/2 and the like), so G is a linear
+// function of the masked sums of only 3 + 6k functions of t:
+//   x_t itself               (1, t', s_1, c_1, ..., s_k, c_k)        K = 2 + 2k
+//   t'^2
+//   s_j, c_j for j = k+1..2k (the sum frequencies)
+//   t' s_j, t' c_j for j = 1..k
+// where s_j = sin(2 pi j t / f), c_j = cos(2 pi j t / f) and t' = (t - c)/s
+// is the centred and scaled trend.  A basis row holds these values for one
+// date, x_t first, padded to a multiple of 4 floats.
+// ---------------------------------------------------------------------------
+template <int KH>
+struct Basis {
+    static constexpr int K = 2 + 2 * KH;
+    static constexpr int NBR = 3 + 6 * KH;       // live entries
+    static constexpr int NB = (NBR + 3) & ~3;    // row stride (floats)
+    static constexpr int TT = K;                 // t'^2
+    __host__ __device__ static constexpr int S(int j) { return j <= KH ? 2 + 2 * (j - 1) : K + 1 + 2 * (j - KH - 1); }
+    __host__ __device__ static constexpr int C(int j) { return S(j) + 1; }
+    __host__ __device__ static constexpr int TS(int j) { return K + 1 + 2 * KH + 2 * (j - 1); }
+    __host__ __device__ static constexpr int TC(int j) { return TS(j) + 1; }
+};
+
+inline int basis_stride(int kh) {
+    return kh == 1 ? Basis<1>::NB : kh == 2 ? Basis<2>::NB : Basis<3>::NB;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel arguments
+// ---------------------------------------------------------------------------
+struct MonitorParams {
+    const void* Y;            // [N][m] time-major
+    const uint32_t* mask;     // [N][mask_words] or null
+    int64_t m;
+    int64_t mask_words;       // ceil(m/32)
+    int N;
+    int n_hist;
+    const float* basis;       // [N][NB]
+    double h_frac;
+    float lambda;
+    float c_over_s;           // trend centring, to map beta back to raw t
+    float inv_s;
+    int box_rows;             // TMA box height (dates per box)
+    int nbox;                 // boxes per tile (nbox * box_rows >= N)
+    int ring;                 // residual ring length (power of two), 0 = in place
+    int32_t* brk;
+    float* mean;
+    float* sigma;
+    float* beta;              // [K][m]
+    uint8_t* status;
+};
+
+// Each kernel translation unit keeps its own device error word (bit 0: a
+// tile-load wait gave up); these read and clear it, synchronising `s`.
+cudaError_t simt_read_clear_errors(cudaStream_t s, unsigned int* bits);
+
+}  // namespace bfm
+
+// ---------------------------------------------------------------------------
+// Public design handle
+// ---------------------------------------------------------------------------
+struct bfm_design_s {
+    int N = 0, k = 0, K = 0;
+    double f = 0.0;
+    std::vector<double> dates;
+    double c = 0.0, s = 1.0;  // trend centring/scaling
+    int NB = 0;               // basis row stride (floats)
+    float* d_basis = nullptr; // device [N][NB]
+    int device = -1;
+    int refcount = 0;
+    uint64_t key = 0;
+};
+
+namespace bfm {
+
+void set_error(const std::string& msg);
+bfm_status cuda_fail(cudaError_t e, const char* what);
+
+// Launch the CUDA-core (SIMT) kernel for one tile set on `stream`.
+bfm_status launch_simt(const bfm_design_s* d, const void* Y, int dtype, const uint32_t* mask, int64_t m,
+                       int n_hist, double h_frac, double lambda, int32_t* brk, float* mean, float* sigma,
+                       float* beta, uint8_t* status, cudaStream_t stream);
+
+// Shared-memory bytes the SIMT kernel needs for a design/dtype/bandwidth, or 0 if too large.
+size_t simt_smem_bytes(int N, int dtype, int n_hist, double h_frac, int* box_rows, int* nbox, int* ring);
+
+}  // namespace bfm

@@ -166,3 +166,88 @@ def tiles_c4(seed: int = 4, count: int = 64, scale: float = 1.0):
         out.append(dict(tile=i, seed=1000 + i, m=max(m, 1), N=N, k=k, n_hist=max(int(hf * N), 2 * k + 3),
                         miss=miss, p_a=p_a, p_b=p_b, h_frac=0.25, f=23.0))
     return out
+
+
+# ---- device-side generation of large scenes ---------------------------------------
+#
+# The full c2 scene (8.4 M pixels x 414 dates) takes minutes through the C
+# generator, so large scenes are drawn on the GPU with PyTorch's seeded
+# generator instead: the same recipe (dates, signal, noise, cloud chain,
+# shifts), different random streams.  Tests that check such a scene against
+# the oracle copy the sampled pixel columns back from the device.
+
+_TORCH_CHUNK = 1 << 22
+
+
+def scene_torch(*, seed: int, m: int, N: int, n_hist: int, f: float = 23.0, k_gen: int = 3,
+                intercept: float = 0.5, slope: float = 0.0, coef_fixed=None, coef_umax: float = 0.3,
+                noise_sd: float = 0.04, miss: str = "markov", p_a: float = 0.25, p_b: float = 0.375,
+                break_frac: float = 0.1, step=(-0.5, -0.1), dtype: str = "f32", device="cuda",
+                date_vals=None):
+    """Generate a scene directly in device memory.  Returns (dates numpy,
+    Y [N][m] tensor, true_break [m] int32 tensor).  Deterministic for a given
+    (seed, m): pixel chunks of 2^22 get their own generator seed."""
+    import torch
+    d = dates(seed, N) if date_vals is None else np.ascontiguousarray(date_vals, dtype=np.float64)
+    tt = np.asarray(d)
+    harm = np.empty((N, 2 * k_gen))
+    for j in range(1, k_gen + 1):
+        harm[:, 2 * (j - 1)] = np.sin(2 * np.pi * j * tt / f)
+        harm[:, 2 * (j - 1) + 1] = np.cos(2 * np.pi * j * tt / f)
+    harm_t = torch.from_numpy(harm.astype(np.float32)).to(device)
+    base_t = torch.from_numpy((intercept + slope * tt).astype(np.float32)).to(device)
+    tdtype = torch.float32 if dtype == "f32" else torch.int16
+    Y = torch.empty((N, m), dtype=tdtype, device=device)
+    brk = torch.empty(m, dtype=torch.int32, device=device)
+    pi_miss = p_b / (p_a + p_b) if (p_a + p_b) > 0 else 0.0
+    for ci, c0 in enumerate(range(0, m, _TORCH_CHUNK)):
+        mc = min(_TORCH_CHUNK, m - c0)
+        g = torch.Generator(device=device)
+        g.manual_seed((seed * 1000003 + ci * 7919 + 17) % (2**63 - 1))
+        if coef_fixed is not None:
+            coef = torch.tensor(coef_fixed, dtype=torch.float32, device=device).expand(mc, 2 * k_gen)
+        else:
+            coef = torch.rand((mc, 2 * k_gen), generator=g, device=device) * coef_umax
+        is_b = torch.rand(mc, generator=g, device=device) < break_frac
+        span = N - n_hist
+        bd = n_hist + torch.floor(torch.rand(mc, generator=g, device=device) * span).to(torch.int32)
+        bd = torch.clamp(bd, max=N - 1)
+        stp = step[0] + (step[1] - step[0]) * torch.rand(mc, generator=g, device=device)
+        bdate = torch.where(is_b & (span > 0), bd, torch.full_like(bd, -1))
+        brk[c0:c0 + mc] = bdate
+        state = torch.rand(mc, generator=g, device=device) < pi_miss if miss == "markov" else None
+        sig = coef @ harm_t.T  # [mc, N]
+        for t in range(N):
+            if miss == "markov":
+                if t > 0:
+                    u = torch.rand(mc, generator=g, device=device)
+                    state = torch.where(state, ~(u < p_a), u < p_b)
+                mt = state
+            elif miss == "iid":
+                mt = torch.rand(mc, generator=g, device=device) < p_a
+            else:
+                mt = None
+            y = base_t[t] + sig[:, t] + noise_sd * torch.randn(mc, generator=g, device=device)
+            y = y + torch.where((bdate >= 0) & (t >= bdate), stp, torch.zeros_like(stp))
+            if dtype == "f32":
+                if mt is not None:
+                    y = torch.where(mt, torch.full_like(y, float("nan")), y)
+                Y[t, c0:c0 + mc] = y
+            else:
+                v = torch.clamp(torch.round(y * 1e4), -32767, 32767).to(torch.int16)
+                if mt is not None:
+                    v = torch.where(mt, torch.full_like(v, -32768), v)
+                Y[t, c0:c0 + mc] = v
+        del sig
+    return d, Y, brk
+
+
+def workload_torch(name: str, *, m: int | None = None, device="cuda", dtype: str | None = None):
+    """Device-resident version of :func:`workload` (same recipe, torch streams)."""
+    w = WORKLOADS[name]
+    mm = w["m"] if m is None else int(m)
+    dt = w["dtype"] if dtype is None else dtype
+    d, Y, brk = scene_torch(seed=w["seed"], m=mm, N=w["N"], n_hist=w["n_hist"], f=w["f"], dtype=dt,
+                            device=device, **w["gen"])
+    return dict(name=name, dates=d, Y=Y, true_break=brk, m=mm, N=w["N"], n_hist=w["n_hist"], f=w["f"],
+                k=w["k"], h_frac=w["h_frac"], lam=workload_lambda(name), dtype=dt)
