@@ -24,6 +24,7 @@
 
 #include "bfm_internal.cuh"
 #include "ptx.cuh"
+#include "simt_pixel.cuh"
 
 namespace bfm {
 
@@ -44,9 +45,6 @@ cudaError_t simt_read_clear_errors(cudaStream_t s, unsigned int* bits) {
 namespace {
 
 constexpr uint64_t kLoadWaitLimitNs = 2000000000ull;  // 2 s
-constexpr float kSingularRatio = 1e-5f;
-constexpr float kDegenerateRatio = 1e-6f;
-constexpr double kE = 2.71828182845904523536;
 
 template <typename T>
 struct Obs;
@@ -70,16 +68,6 @@ struct Obs<int16_t> {
     }
     static __device__ __forceinline__ int16_t missing() { return (int16_t)-32768; }
 };
-
-// Compensated (Neumaier) accumulation s += x with error term c.
-__device__ __forceinline__ void comp_add(float& s, float& c, float x) {
-    float t = s + x;
-    if (fabsf(s) >= fabsf(x))
-        c += (s - t) + x;
-    else
-        c += (x - t) + s;
-    s = t;
-}
 
 template <int KH>
 __device__ __forceinline__ void load_row(const float4* __restrict__ B4, int t, float (&q)[Basis<KH>::NB]) {
@@ -110,89 +98,10 @@ __device__ __forceinline__ void load_x(const float4* __restrict__ B4, int t, flo
     for (int i = 0; i < K; ++i) x[i] = q[i];
 }
 
-// Gram matrix from the masked basis sums a[] (see Basis).
-template <int KH>
-__device__ __forceinline__ void gram_from_sums(const float (&a)[Basis<KH>::NBR], float (&G)[Basis<KH>::K][Basis<KH>::K]) {
-    using B = Basis<KH>;
-    auto Cs = [&](int j) -> float { return j == 0 ? a[0] : a[B::C(j)]; };
-    auto Ss = [&](int j) -> float { return j == 0 ? 0.f : (j > 0 ? a[B::S(j)] : -a[B::S(-j)]); };
-    G[0][0] = a[0];
-    G[0][1] = a[1];
-    G[1][1] = a[B::TT];
-#pragma unroll
-    for (int j = 1; j <= KH; ++j) {
-        G[0][B::S(j)] = a[B::S(j)];
-        G[0][B::C(j)] = a[B::C(j)];
-        G[1][B::S(j)] = a[B::TS(j)];
-        G[1][B::C(j)] = a[B::TC(j)];
-#pragma unroll
-        for (int b = 1; b <= KH; ++b) {
-            int dm = j > b ? j - b : b - j;
-            G[B::S(j)][B::S(b)] = 0.5f * (Cs(dm) - Cs(j + b));
-            G[B::C(j)][B::C(b)] = 0.5f * (Cs(dm) + Cs(j + b));
-            G[B::S(j)][B::C(b)] = 0.5f * (Ss(j + b) + Ss(j - b));
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < B::K; ++i)
-#pragma unroll
-        for (int j = 0; j < i; ++j) G[i][j] = G[j][i];
-    // the sin/cos blocks were written for all (j, b); make them symmetric too
-#pragma unroll
-    for (int i = 0; i < B::K; ++i)
-#pragma unroll
-        for (int j = i + 1; j < B::K; ++j) G[j][i] = G[i][j];
-}
-
-// In-register Cholesky G = L L' (lower, reciprocal diagonal kept in dinv).
-// Returns false when a pivot relative to its diagonal entry is below kSingularRatio.
-template <int K>
-__device__ __forceinline__ bool cholesky(const float (&G)[K][K], float (&L)[K][K], float (&dinv)[K]) {
-    bool ok = true;
-#pragma unroll
-    for (int j = 0; j < K; ++j) {
-        float d = G[j][j];
-#pragma unroll
-        for (int c = 0; c < j; ++c) d = fmaf(-L[j][c], L[j][c], d);
-        ok = ok && (d >= kSingularRatio * G[j][j]) && (G[j][j] > 0.f);
-        float inv = rsqrtf(fmaxf(d, 1e-30f));
-        dinv[j] = inv;
-        L[j][j] = d * inv;
-#pragma unroll
-        for (int i = j + 1; i < K; ++i) {
-            float s = G[i][j];
-#pragma unroll
-            for (int c = 0; c < j; ++c) s = fmaf(-L[i][c], L[j][c], s);
-            L[i][j] = s * inv;
-        }
-    }
-    return ok;
-}
-
-template <int K>
-__device__ __forceinline__ void chol_solve(const float (&L)[K][K], const float (&dinv)[K], const float (&b)[K],
-                                           float (&x)[K]) {
-    float z[K];
-#pragma unroll
-    for (int i = 0; i < K; ++i) {
-        float s = b[i];
-#pragma unroll
-        for (int c = 0; c < i; ++c) s = fmaf(-L[i][c], z[c], s);
-        z[i] = s * dinv[i];
-    }
-#pragma unroll
-    for (int i = K - 1; i >= 0; --i) {
-        float s = z[i];
-#pragma unroll
-        for (int c = i + 1; c < K; ++c) s = fmaf(-L[c][i], x[c], s);
-        x[i] = s * dinv[i];
-    }
-}
-
 template <int KH, typename T, bool kTMA>
 __global__ void __launch_bounds__(32) simt_kernel(const __grid_constant__ CUtensorMap tmap, const MonitorParams P) {
     using B = Basis<KH>;
-    constexpr int K = B::K, NB = B::NB, NBR = B::NBR;
+    constexpr int K = B::K, NB = B::NB;
     constexpr bool kInPlace = sizeof(T) == sizeof(float);
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -207,7 +116,7 @@ __global__ void __launch_bounds__(32) simt_kernel(const __grid_constant__ CUtens
     const int64_t p0 = (int64_t)blockIdx.x * 32;
     const int64_t p = p0 + lane;
     const bool active = p < P.m;
-    const int N = P.N, n_hist = P.n_hist;
+    const int N = P.N;
 
     // ---- stage the [N][32] tile -------------------------------------------------
     if constexpr (kTMA) {
@@ -242,72 +151,11 @@ __global__ void __launch_bounds__(32) simt_kernel(const __grid_constant__ CUtens
         if (mrow) v = v && ((__ldg(mrow + (size_t)t * P.mask_words) >> lane) & 1u);
         return v;
     };
-
-    // ---- pass 1: masked basis sums and X'My over the history ---------------------
-    float a[NBR], bb[K];
-#pragma unroll
-    for (int i = 0; i < NBR; ++i) a[i] = 0.f;
-#pragma unroll
-    for (int i = 0; i < K; ++i) bb[i] = 0.f;
-    float ymax = 0.f;
-#pragma unroll 2
-    for (int t = 0; t < n_hist; ++t) {
-        float y;
-        bool v = obs(t, y);
-        float w = v ? 1.f : 0.f, yw = v ? y : 0.f;
-        ymax = fmaxf(ymax, fabsf(yw));
-        float q[NB];
-        load_row<KH>(B4, t, q);
-        a[0] += w;
-#pragma unroll
-        for (int l = 1; l < NBR; ++l) a[l] = fmaf(w, q[l], a[l]);
-        bb[0] += yw;
-#pragma unroll
-        for (int i = 1; i < K; ++i) bb[i] = fmaf(yw, q[i], bb[i]);
-    }
-    const int n_i = (int)a[0];
-
-    // ---- solve ---------------------------------------------------------------------
-    float G[K][K], L[K][K], dinv[K], beta[K];
-    gram_from_sums<KH>(a, G);
-    const bool nonsingular = cholesky<K>(G, L, dinv);
-    chol_solve<K>(L, dinv, bb, beta);
-
-    // ---- pass 1b: one refinement step ------------------------------------------------
-    {
-        float cc[K];
-#pragma unroll
-        for (int i = 0; i < K; ++i) cc[i] = 0.f;
-#pragma unroll 2
-        for (int t = 0; t < n_hist; ++t) {
-            float y;
-            bool v = obs(t, y);
-            float x[K];
-            load_x<KH>(B4, t, x);
-            float f0 = 0.f, f1 = 0.f;
-#pragma unroll
-            for (int i = 0; i < K; i += 2) {
-                f0 = fmaf(x[i], beta[i], f0);
-                f1 = fmaf(x[i + 1], beta[i + 1], f1);
-            }
-            float r = v ? (y - (f0 + f1)) : 0.f;
-#pragma unroll
-            for (int i = 0; i < K; ++i) cc[i] = fmaf(r, x[i], cc[i]);
-        }
-        float dl[K];
-        chol_solve<K>(L, dinv, cc, dl);
-#pragma unroll
-        for (int i = 0; i < K; ++i) beta[i] += dl[i];
-    }
-
-    int h = (int)floor(P.h_frac * (double)n_i);
-    if (h < 1) h = 1;
-    if (h > n_i) h = n_i;  // 0 when n_i = 0: every index below stays >= 0
-    const int wstart = n_i - h;  // first compacted index inside the first window
-
+    auto row = [&](int t, float (&q)[NB]) { load_row<KH>(B4, t, q); };
+    auto rowx = [&](int t, float (&x)[K]) { load_x<KH>(B4, t, x); };
     auto store_r = [&](int j, float r) {
         if constexpr (kInPlace)
-            reinterpret_cast<float*>(tile)[j * 32 + lane] = r;
+            reinterpret_cast<float*>(tile)[j * 32 + lane] = r;  // j <= t: overwrites consumed dates only
         else
             ring[(j & (P.ring - 1)) * 32 + lane] = r;
     };
@@ -318,105 +166,17 @@ __global__ void __launch_bounds__(32) simt_kernel(const __grid_constant__ CUtens
             return ring[(j & (P.ring - 1)) * 32 + lane];
     };
 
-    // ---- pass 2a: history residuals, sigma-hat, first window -------------------------
-    int j = 0;
-    float ss = 0.f, W = 0.f, Wc = 0.f;
-#pragma unroll 2
-    for (int t = 0; t < n_hist; ++t) {
-        float y;
-        bool v = obs(t, y);
-        float x[K];
-        load_x<KH>(B4, t, x);
-        float f0 = 0.f, f1 = 0.f;
-#pragma unroll
-        for (int i = 0; i < K; i += 2) {
-            f0 = fmaf(x[i], beta[i], f0);
-            f1 = fmaf(x[i + 1], beta[i + 1], f1);
-        }
-        float r = y - (f0 + f1);
-        if (v) {
-            ss = fmaf(r, r, ss);
-            store_r(j, r);
-            if (j >= wstart) comp_add(W, Wc, r);
-            ++j;
-        }
-    }
-    const float sigma = sqrtf(ss / (float)(n_i - K));
-    const bool degenerate = !(sigma > kDegenerateRatio * ymax) || ymax == 0.f;
-    const float scale = sigma * sqrtf((float)n_i);
-    const float thr = P.lambda * scale;
-    const int jlim = (int)floor(kE * (double)n_i);  // j/n_i <= e  <=>  j <= jlim
-
-    // ---- pass 2b: monitoring MOSUM, first crossing, mean ------------------------------
-    int brk = -1;
-    float sumW = 0.f, sumWc = 0.f;
-#pragma unroll 2
-    for (int t = n_hist; t < N; ++t) {
-        float y;
-        bool v = obs(t, y);
-        float x[K];
-        load_x<KH>(B4, t, x);
-        float f0 = 0.f, f1 = 0.f;
-#pragma unroll
-        for (int i = 0; i < K; i += 2) {
-            f0 = fmaf(x[i], beta[i], f0);
-            f1 = fmaf(x[i + 1], beta[i + 1], f1);
-        }
-        float r = y - (f0 + f1);
-        if (v) {
-            float lag = load_r(j - h);
-            store_r(j, r);
-            comp_add(W, Wc, r - lag);
-            const float wv = W + Wc;
-            const int J = j + 1;  // 1-based monitoring position
-            float th = thr;
-            if (J > jlim) th = thr * sqrtf(logf((float)J / (float)n_i));
-            if (brk < 0 && fabsf(wv) > th) brk = t;
-            comp_add(sumW, sumWc, wv);
-            ++j;
-        }
-    }
-    const int N_i = j;
+    PixelParams pp{P.N, P.n_hist, P.h_frac, P.lambda, P.c_over_s, P.inv_s};
+    PixelOut<KH> o;
+    process_pixel<KH>(pp, obs, row, rowx, store_r, load_r, o);
 
     if (!active) return;
-    uint8_t st;
-    float o_mean, o_sigma = sigma;
-    int o_brk = -1;
-    bool fitted = true;
-    if (n_i <= K) {
-        st = BFM_PX_INSUFFICIENT_HISTORY;
-        fitted = false;
-    } else if (!nonsingular) {
-        st = BFM_PX_SINGULAR;
-        fitted = false;
-    } else if (degenerate) {
-        st = BFM_PX_DEGENERATE;
-        o_mean = 0.f;
-    } else if (N_i == n_i) {
-        st = BFM_PX_NO_MONITOR;
-        o_mean = __int_as_float(0x7fc00000);
-    } else {
-        st = BFM_PX_OK;
-        o_brk = brk;
-        o_mean = (sumW + sumWc) / ((float)(N_i - n_i) * scale);
-    }
-    const float qnan = __int_as_float(0x7fc00000);
-    if (!fitted) {
-        o_mean = qnan;
-        o_sigma = qnan;
-    }
-    P.status[p] = st;
-    P.brk[p] = o_brk;
-    P.mean[p] = o_mean;
-    P.sigma[p] = o_sigma;
-    // beta of the centred trend -> raw parameterisation of Eq. 2
-    float braw[K];
+    P.status[p] = o.status;
+    P.brk[p] = o.brk;
+    P.mean[p] = o.mean;
+    P.sigma[p] = o.sigma;
 #pragma unroll
-    for (int i = 0; i < K; ++i) braw[i] = beta[i];
-    braw[0] = fmaf(-beta[1], P.c_over_s, beta[0]);
-    braw[1] = beta[1] * P.inv_s;
-#pragma unroll
-    for (int i = 0; i < K; ++i) P.beta[(size_t)i * P.m + p] = fitted ? braw[i] : qnan;
+    for (int i = 0; i < K; ++i) P.beta[(size_t)i * P.m + p] = o.beta[i];
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
