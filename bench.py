@@ -105,18 +105,20 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_rate(w_np_Y, dates, k, f, n_hist, h_frac, lam, budget_s: float):
-    """Time the oracle on a bounded sample (columns of the same scene)."""
+def cpu_oracle_rate(Y_host, dates, k, f, n_hist, h_frac, lam, budget_s: float):
+    """Time the oracle on a bounded sample: successive blocks of pixel
+    columns of the same scene until about budget_s seconds of work."""
     import oracle
-    m_all = w_np_Y.shape[1]
-    cal = min(1024, m_all)
-    t0 = time.perf_counter()
-    oracle.monitor(dates, w_np_Y[:, :cal], k=k, f=f, n_hist=n_hist, h_frac=h_frac, lam=lam)
-    rate = cal / (time.perf_counter() - t0)
-    n = int(min(m_all, max(cal, rate * budget_s)))
-    t0 = time.perf_counter()
-    oracle.monitor(dates, w_np_Y[:, :n], k=k, f=f, n_hist=n_hist, h_frac=h_frac, lam=lam)
-    dt = time.perf_counter() - t0
+    m_all = Y_host.shape[1]
+    blk = min(1 << 16, m_all)
+    n, dt, c0 = 0, 0.0, 0
+    while dt < budget_s and n < m_all:
+        cols = np.ascontiguousarray(Y_host[:, c0:c0 + blk].numpy())
+        t0 = time.perf_counter()
+        oracle.monitor(dates, cols, k=k, f=f, n_hist=n_hist, h_frac=h_frac, lam=lam)
+        dt += time.perf_counter() - t0
+        n += cols.shape[1]
+        c0 += blk
     return n / dt, n, dt
 
 
@@ -169,7 +171,7 @@ def run_ours(args):
     bfm.load()
 
     name = "c2"
-    w = synth.workload_torch(name, device=dev, dtype="f32")
+    w = synth.workload_torch(name, device=dev, dtype="f32", m=args.pixels)
     m, N, n_hist, K = w["m"], w["N"], w["n_hist"], 8
     Y = w["Y"]
     form = args.form
@@ -253,13 +255,13 @@ def run_ours(args):
         e2e = {"value": ws * m / (e_ms / 1e3), "unit": "pixels/s", "h2d_bytes_per_step": N * m * elt,
                "d2h_bytes_per_step": m * (4 + 4 + 4 + 4 * K + 1), "ms_per_step": e_ms,
                "api": "bfm_monitor_host (pinned host Y and outputs, 1 Mi-pixel chunks)"}
-        Ynp = Yh[:, :1 << 17].numpy().copy()
+        Ysrc = Yh
     else:
-        Ynp = Y[:, :1 << 17].cpu().numpy()
+        Ysrc = Y[:, :1 << 20].cpu()
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rate, n, dt = cpu_oracle_rate(Ynp, w["dates"], 3, 23.0, n_hist, w["h_frac"], w["lam"], budget_s=15.0)
+        rate, n, dt = cpu_oracle_rate(Ysrc, w["dates"], 3, 23.0, n_hist, w["h_frac"], w["lam"], budget_s=15.0)
         cpu = {"value": rate, "unit": "pixels/s", "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count())),
                "kind": "oracle", "sample": f"first {n} pixels of the same scene, all {N} dates, FP64 oracle ({dt:.1f} s)"}
 
@@ -268,7 +270,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "pixels/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if form == "f32" else "i16", "data": "synthetic",
-        "config": {"workload": WORKLOAD if form == "f32" else WORKLOAD.replace("plain float32", "int16 storage"),
+        "config": {"workload": (WORKLOAD if form == "f32" else WORKLOAD.replace("plain float32", "int16 storage"))
+                   if args.pixels is None else f"c2 recipe with {m} pixels (profiling case)",
                    "pixels": m, "dates": N, "n_hist": n_hist, "K": K, "form": form,
                    "algo": "simt", "l2": "inputs larger than L2 (Y is %.1f GB per step)" % (N * m * elt / 1e9),
                    "parallelism": f"{ws} independent scene(s), one per GPU"},
@@ -294,6 +297,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="f32", choices=["f32", "i16"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--pixels", type=int, default=None,
+                    help="fewer pixels of the same recipe (profiling captures only; not a bench line)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

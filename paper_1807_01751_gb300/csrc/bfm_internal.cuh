@@ -60,7 +60,6 @@ struct MonitorParams {
     float inv_s;
     int box_rows;             // TMA box height (dates per box)
     int nbox;                 // boxes per tile (nbox * box_rows >= N)
-    int ring;                 // residual ring length (power of two), 0 = in place
     int32_t* brk;
     float* mean;
     float* sigma;
@@ -99,7 +98,7 @@ bfm_status launch_simt(const bfm_design_s* d, const void* Y, int dtype, const ui
                        int n_hist, double h_frac, double lambda, int32_t* brk, float* mean, float* sigma,
                        float* beta, uint8_t* status, cudaStream_t stream);
 
-// Shared-memory bytes the SIMT kernel needs for a design/dtype/bandwidth, or 0 if too large.
-size_t simt_smem_bytes(int N, int dtype, int n_hist, double h_frac, int* box_rows, int* nbox, int* ring);
+// Shared-memory bytes the SIMT kernel needs for N dates, k harmonics and a dtype (0 if too large).
+size_t simt_smem_bytes(int N, int k, int dtype, int* box_rows, int* nbox);
 
 }  // namespace bfm

@@ -24,7 +24,7 @@
 
 #include "bfm_internal.cuh"
 #include "ptx.cuh"
-#include "simt_pixel.cuh"
+#include "simt_seg.cuh"
 
 namespace bfm {
 
@@ -99,53 +99,57 @@ __device__ __forceinline__ void load_x(const float4* __restrict__ B4, int t, flo
 }
 
 template <int KH, typename T, bool kTMA>
-__global__ void __launch_bounds__(32) simt_kernel(const __grid_constant__ CUtensorMap tmap, const MonitorParams P) {
+__global__ void __launch_bounds__(kNW * 32) simt_kernel(const __grid_constant__ CUtensorMap tmap, const MonitorParams P) {
     using B = Basis<KH>;
-    constexpr int K = B::K, NB = B::NB;
+    constexpr int K = B::K, NB = B::NB, PS = Partials<KH>::kStride;
     constexpr bool kInPlace = sizeof(T) == sizeof(float);
 
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T* tile = reinterpret_cast<T*>(smem_raw);
     const int rows = P.nbox * P.box_rows;
     const size_t tile_bytes = ((size_t)rows * 32 * sizeof(T) + 127) & ~(size_t)127;
-    float* ring = reinterpret_cast<float*>(smem_raw + tile_bytes);
-    const size_t ring_bytes = (size_t)P.ring * 32 * sizeof(float);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + tile_bytes + ring_bytes);
+    const size_t work_bytes = kInPlace ? 0 : (((size_t)P.N * 32 * sizeof(float) + 127) & ~(size_t)127);
+    float* work = kInPlace ? reinterpret_cast<float*>(smem_raw) : reinterpret_cast<float*>(smem_raw + tile_bytes);
+    float* part = reinterpret_cast<float*>(smem_raw + tile_bytes + work_bytes);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(part + kNW * PS * 32);
 
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
     const int64_t p0 = (int64_t)blockIdx.x * 32;
     const int64_t p = p0 + lane;
     const bool active = p < P.m;
     const int N = P.N;
 
-    // ---- stage the [N][32] tile -------------------------------------------------
+    // ---- stage the [N][32] tile -------------------------------------------------------
     if constexpr (kTMA) {
-        if (lane == 0) {
+        if (threadIdx.x == 0) {
             ptx::prefetch_tmap(&tmap);
             ptx::mbar_init(bar, 1);
             ptx::fence_mbar_init();
         }
-        __syncwarp();
-        if (lane == 0) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
             ptx::mbar_arrive_expect_tx(bar, (uint32_t)(rows * 32 * sizeof(T)));
             for (int b = 0; b < P.nbox; ++b)
                 ptx::tma_load_2d(tile + (size_t)b * P.box_rows * 32, &tmap, bar, (int)p0, b * P.box_rows);
         }
         if (!ptx::mbar_wait_bounded(bar, 0, kLoadWaitLimitNs)) {
-            if (lane == 0) atomicOr(&g_bfm_err, 1u);
-            if (active) P.status[p] = BFM_PX_TIMEOUT;
+            if (threadIdx.x == 0) atomicOr(&g_bfm_err, 1u);
+            if (w == 0 && active) P.status[p] = BFM_PX_TIMEOUT;
             ptx::mbar_wait_bounded(bar, 0, kLoadWaitLimitNs);  // let copies in flight land
             return;
         }
     } else {
         const T* Yp = reinterpret_cast<const T*>(P.Y);
-        for (int t = 0; t < N; ++t) tile[t * 32 + lane] = active ? Yp[(size_t)t * P.m + p] : Obs<T>::missing();
-        __syncwarp();
+        for (int idx = threadIdx.x; idx < N * 32; idx += kNW * 32) {
+            const int t = idx >> 5, l = idx & 31;
+            tile[idx] = (p0 + l < P.m) ? Yp[(size_t)t * P.m + p0 + l] : Obs<T>::missing();
+        }
+        __syncthreads();
     }
 
     const float4* B4 = reinterpret_cast<const float4*>(P.basis);
     const uint32_t* mrow = P.mask ? P.mask + blockIdx.x : nullptr;
-
     auto obs = [&](int t, float& y) -> bool {
         bool v = Obs<T>::get(tile, t * 32 + lane, y);
         if (mrow) v = v && ((__ldg(mrow + (size_t)t * P.mask_words) >> lane) & 1u);
@@ -153,23 +157,35 @@ __global__ void __launch_bounds__(32) simt_kernel(const __grid_constant__ CUtens
     };
     auto row = [&](int t, float (&q)[NB]) { load_row<KH>(B4, t, q); };
     auto rowx = [&](int t, float (&x)[K]) { load_x<KH>(B4, t, x); };
-    auto store_r = [&](int j, float r) {
-        if constexpr (kInPlace)
-            reinterpret_cast<float*>(tile)[j * 32 + lane] = r;  // j <= t: overwrites consumed dates only
-        else
-            ring[(j & (P.ring - 1)) * 32 + lane] = r;
-    };
-    auto load_r = [&](int j) -> float {
-        if constexpr (kInPlace)
-            return reinterpret_cast<float*>(tile)[j * 32 + lane];
-        else
-            return ring[(j & (P.ring - 1)) * 32 + lane];
-    };
+    auto partf = [&](int ww, int i) -> float& { return part[(ww * PS + i) * 32 + lane]; };
+    auto put_r = [&](int t, float r) { work[t * 32 + lane] = r; };
+    auto get_r = [&](int t) -> float { return work[t * 32 + lane]; };
+    auto putw = [&](int ww, int i, uint32_t bits) { partf(ww, 3 + i) = __uint_as_float(bits); };
+    auto getw = [&](int ww, int i) -> uint32_t { return __float_as_uint(partf(ww, 3 + i)); };
 
-    PixelParams pp{P.N, P.n_hist, P.h_frac, P.lambda, P.c_over_s, P.inv_s};
+    const SegParams sp{P.N, P.n_hist, P.h_frac, P.lambda, P.c_over_s, P.inv_s};
+    Lane<KH> S;
+    phase1_gram<KH>(sp, w, obs, row, partf);
+    __syncthreads();
+    phase2_solve<KH>(S, partf);
+    __syncthreads();
+    phase3_refine<KH>(sp, w, S, obs, rowx, partf);
+    __syncthreads();
+    phase4_sigma<KH>(sp, S, partf);
+    __syncthreads();
+    phase5_resid<KH>(sp, w, S, obs, rowx, put_r, partf);
+    __syncthreads();
+    phase6_prefix<KH>(sp, w, S, get_r, put_r, partf, putw);
+    __syncthreads();
+    int first_mon = S.n_i - S.myoff;
+    first_mon = first_mon < 0 ? 0 : first_mon;
+    const int jlo = __reduce_min_sync(0xffffffffu, first_mon);
+    const int jhi = __reduce_max_sync(0xffffffffu, S.mycnt);
+    phase7_mosum<KH>(sp, w, S, get_r, jlo, jhi, partf, getw);
+    __syncthreads();
+    if (w != 0) return;
     PixelOut<KH> o;
-    process_pixel<KH>(pp, obs, row, rowx, store_r, load_r, o);
-
+    phase8_out<KH>(sp, S, partf, o);
     if (!active) return;
     P.status[p] = o.status;
     P.brk[p] = o.brk;
@@ -206,7 +222,7 @@ bfm_status launch_one(const CUtensorMap& tm, const MonitorParams& P, size_t smem
         configured_dev = dev;
     }
     const unsigned grid = (unsigned)((P.m + 31) / 32);
-    kern<<<grid, 32, smem, stream>>>(tm, P);
+    kern<<<grid, kNW * 32, smem, stream>>>(tm, P);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "simt kernel launch");
     return BFM_OK;
@@ -222,24 +238,18 @@ bfm_status dispatch_dtype(int dtype, bool tma, const CUtensorMap& tm, const Moni
 
 }  // namespace
 
-size_t simt_smem_bytes(int N, int dtype, int n_hist, double h_frac, int* box_rows, int* nbox, int* ring) {
+size_t simt_smem_bytes(int N, int k, int dtype, int* box_rows, int* nbox) {
     const int elt = dtype == BFM_F32 ? 4 : 2;
     const int nb = (N + 255) / 256;
     const int br = (N + nb - 1) / nb;
     const int rows = nb * br;
-    size_t tile = ((size_t)rows * 32 * elt + 127) & ~(size_t)127;
-    int rg = 0;
-    if (dtype != BFM_F32) {
-        int hmax = (int)std::floor(h_frac * (double)n_hist);
-        if (hmax < 1) hmax = 1;
-        if (hmax > n_hist) hmax = n_hist;
-        rg = 1;
-        while (rg < hmax + 1) rg <<= 1;
-    }
-    size_t total = tile + (size_t)rg * 32 * 4 + 16;
+    const size_t tile = ((size_t)rows * 32 * elt + 127) & ~(size_t)127;
+    const size_t work = dtype == BFM_F32 ? 0 : (((size_t)N * 32 * 4 + 127) & ~(size_t)127);
+    const int ps = k == 1 ? Partials<1>::kStride : k == 2 ? Partials<2>::kStride : Partials<3>::kStride;
+    const size_t total = tile + work + (size_t)kNW * ps * 32 * 4 + 16;
     if (box_rows) *box_rows = br;
     if (nbox) *nbox = nb;
-    if (ring) *ring = rg;
+    if ((N + kNW - 1) / kNW > 32 * kSegWords) return 0;
     return total <= 227 * 1024 ? total : 0;
 }
 
@@ -247,8 +257,8 @@ bfm_status launch_simt(const bfm_design_s* d, const void* Y, int dtype, const ui
                        double h_frac, double lambda, int32_t* brk, float* mean, float* sigma, float* beta,
                        uint8_t* status, cudaStream_t stream) {
     MonitorParams P{};
-    int br = 0, nb = 0, rg = 0;
-    size_t smem = simt_smem_bytes(d->N, dtype, n_hist, h_frac, &br, &nb, &rg);
+    int br = 0, nb = 0;
+    size_t smem = simt_smem_bytes(d->N, d->k, dtype, &br, &nb);
     if (smem == 0) {
         set_error("bfm_monitor: the series does not fit one on-chip tile (N or the bandwidth too large)");
         return BFM_EUNSUPPORTED;
@@ -266,7 +276,6 @@ bfm_status launch_simt(const bfm_design_s* d, const void* Y, int dtype, const ui
     P.inv_s = (float)(1.0 / d->s);
     P.box_rows = br;
     P.nbox = nb;
-    P.ring = rg;
     P.brk = brk;
     P.mean = mean;
     P.sigma = sigma;
