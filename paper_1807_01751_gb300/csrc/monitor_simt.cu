@@ -98,7 +98,7 @@ __device__ __forceinline__ void load_x(const float4* __restrict__ B4, int t, flo
     for (int i = 0; i < K; ++i) x[i] = q[i];
 }
 
-template <int KH, typename T, bool kTMA>
+template <int KH, typename T, bool kTMA, bool kMask>
 __global__ void __launch_bounds__(kNW * 32) simt_kernel(const __grid_constant__ CUtensorMap tmap, const MonitorParams P) {
     using B = Basis<KH>;
     constexpr int K = B::K, NB = B::NB, PS = Partials<KH>::kStride;
@@ -149,10 +149,10 @@ __global__ void __launch_bounds__(kNW * 32) simt_kernel(const __grid_constant__ 
     }
 
     const float4* B4 = reinterpret_cast<const float4*>(P.basis);
-    const uint32_t* mrow = P.mask ? P.mask + blockIdx.x : nullptr;
+    const uint32_t* mrow = P.mask + blockIdx.x;
     auto obs = [&](int t, float& y) -> bool {
         bool v = Obs<T>::get(tile, t * 32 + lane, y);
-        if (mrow) v = v && ((__ldg(mrow + (size_t)t * P.mask_words) >> lane) & 1u);
+        if constexpr (kMask) v = v && ((__ldg(mrow + (size_t)t * P.mask_words) >> lane) & 1u);
         return v;
     };
     auto row = [&](int t, float (&q)[NB]) { load_row<KH>(B4, t, q); };
@@ -173,10 +173,9 @@ __global__ void __launch_bounds__(kNW * 32) simt_kernel(const __grid_constant__ 
     __syncthreads();
     phase4_sigma<KH>(sp, S, partf);
     __syncthreads();
-    phase5_resid<KH>(sp, w, S, obs, rowx, put_r, partf);
+    phase5_resid<KH>(sp, w, S, obs, rowx, put_r, partf, putw);
     __syncthreads();
-    phase6_prefix<KH>(sp, w, S, get_r, put_r, partf, putw);
-    __syncthreads();
+    phase6_offsets<KH>(w, S, partf);
     int first_mon = S.n_i - S.myoff;
     first_mon = first_mon < 0 ? 0 : first_mon;
     const int jlo = __reduce_min_sync(0xffffffffu, first_mon);
@@ -211,15 +210,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 template <int KH, typename T, bool kTMA>
 bfm_status launch_one(const CUtensorMap& tm, const MonitorParams& P, size_t smem, cudaStream_t stream) {
-    auto kern = simt_kernel<KH, T, kTMA>;
-    static thread_local int configured_dev = -1;
+    auto kern = P.mask ? simt_kernel<KH, T, kTMA, true> : simt_kernel<KH, T, kTMA, false>;
+    static thread_local int configured_dev[2] = {-1, -1};
     int dev = 0;
     cudaGetDevice(&dev);
-    if (configured_dev != dev) {
+    if (configured_dev[P.mask ? 1 : 0] != dev) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(MaxDynamicSharedMemorySize)");
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        configured_dev = dev;
+        configured_dev[P.mask ? 1 : 0] = dev;
     }
     const unsigned grid = (unsigned)((P.m + 31) / 32);
     kern<<<grid, kNW * 32, smem, stream>>>(tm, P);

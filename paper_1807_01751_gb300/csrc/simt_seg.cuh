@@ -16,13 +16,14 @@
 //   4  beta = beta0 + G^-1 c; sum of squared history residuals
 //      s1 = s0 - delta'c (residuals y - x'beta are orthogonal to X), sigma-hat
 //      (Algorithm 1, step 5)                                         [every warp]
-//   5  residuals r = y - x'beta (sign of Eq. 3) at every valid date, kept in
-//      place; per-segment count and sum                              [segments]
-//   6  compacted prefix sums S_J = r_1 + ... + r_J over valid positions J,
-//      stored at the segment's own slots                             [segments]
-//   7  MOSUM MO_J = (S_J - S_{J-h}) / (sigma sqrt(n)) for monitoring J (Eq. 3,
-//      window of h valid residuals), first J with |MO_J| > lambda sqrt(log+(J/n))
-//      (Eq. 4, strict) and the sum of MO_J                          [segments]
+//   5  residuals r = y - x'beta (sign of Eq. 3) at every valid date and their
+//      compacted prefix sums within the segment, stored in the segment's own
+//      slots; segment count, sum and validity words                 [segments]
+//   6  segment offsets (exclusive sums of counts and sums)           [every warp]
+//   7  MOSUM MO_J = (S_J - S_{J-h}) / (sigma sqrt(n)) for monitoring J, with
+//      S_J = r_1 + ... + r_J over valid positions (Eq. 3, window of h valid
+//      residuals); first J with |MO_J| > lambda sqrt(log+(J/n)) (Eq. 4,
+//      strict) and the sum of MO_J                                   [segments]
 //   8  combine: earliest crossing, mean MOSUM, status, outputs       [one warp]
 #pragma once
 
@@ -46,13 +47,11 @@ __host__ __device__ __forceinline__ float qnanf() {
 #endif
 }
 
-// Compensated (Neumaier) accumulation s += x with error term c.
+// Compensated (Kahan) accumulation s += x with error term c (s + c is the sum).
 __host__ __device__ __forceinline__ void comp_add(float& s, float& c, float x) {
-    const float t = s + x;
-    if (fabsf(s) >= fabsf(x))
-        c += (s - t) + x;
-    else
-        c += (x - t) + s;
+    const float y = x + c;
+    const float t = s + y;
+    c = y - (t - s);
     s = t;
 }
 
@@ -184,8 +183,9 @@ struct Lane {
     float sigma, thr, scale;
     int h, jlim;
     // segment bookkeeping of phases 5-7
-    int cnt_off[kNW];  // valid observations before each all-date segment
-    int mycnt, myoff;  // this warp's segment: valid observations, and before it
+    int cnt_off[kNW];                  // valid observations before each all-date segment
+    float sum_off_hi[kNW], sum_off_lo[kNW];  // residual sums before each segment
+    int mycnt, myoff;                  // this warp's segment: valid observations, and before it
     int N_i;
 };
 
@@ -313,16 +313,18 @@ __host__ __device__ __forceinline__ void phase4_sigma(const SegParams& P, Lane<K
     S.jlim = (int)floor(kEuler * (double)n_i);  // J/n_i <= e  <=>  J <= jlim
 }
 
-// ---- phase 5: residuals in place, segment count and sum -------------------------
-// put_r(t, r) stores residual r (NaN for a missing date) at date slot t.
-template <int KH, class Obs, class RowX, class PutR, class Part>
-__host__ __device__ __forceinline__ void phase5_resid(const SegParams& P, int w, Lane<KH>& S, Obs obs, RowX rowx,
-                                                      PutR put_r, Part part) {
+// ---- phase 5: residuals, segment-local compacted prefix sums ------------------------
+// put_s(slot, v) writes slot (always <= the date being read, inside the
+// segment); putw(w, i, bits) stores validity word i of this warp's segment.
+template <int KH, class Obs, class RowX, class PutS, class Part, class PutW>
+__host__ __device__ __forceinline__ void phase5_resid(const SegParams& P, int w, const Lane<KH>& S, Obs obs,
+                                                      RowX rowx, PutS put_s, Part part, PutW putw) {
     constexpr int K = Basis<KH>::K;
     int s0, s1;
     segment(P.N, w, s0, s1);
-    int cnt = 0;
+    int jl = 0;
     float sh = 0.f, sl = 0.f;
+    uint32_t bits = 0u;
 #pragma unroll 2
     for (int t = s0; t < s1; ++t) {
         float y = 0.f;
@@ -330,47 +332,6 @@ __host__ __device__ __forceinline__ void phase5_resid(const SegParams& P, int w,
         float x[K];
         rowx(t, x);
         const float r = y - dot_x<K>(x, S.beta);
-        put_r(t, v ? r : qnanf());
-        if (v) {
-            ++cnt;
-            comp_add(sh, sl, r);
-        }
-    }
-    part(w, 0) = (float)cnt;
-    part(w, 1) = sh;
-    part(w, 2) = sl;
-}
-
-// ---- phase 6: compacted prefix sums in the segment's own slots --------------------
-// get_r(t) reads slot t; put_s(slot, s) writes slot (slot <= current t).
-// putw(w, i, bits) stores validity word i of this warp's segment.
-template <int KH, class GetR, class PutS, class Part, class PutW>
-__host__ __device__ __forceinline__ void phase6_prefix(const SegParams& P, int w, Lane<KH>& S, GetR get_r,
-                                                       PutS put_s, Part part, PutW putw) {
-    int off = 0;
-    float sh = 0.f, sl = 0.f;  // sum of residuals before this warp's segment
-#pragma unroll
-    for (int v = 0; v < kNW; ++v) {
-        const int c = (int)part(v, 0);
-        S.cnt_off[v] = off;
-        if (v == w) {
-            S.mycnt = c;
-            S.myoff = off;
-        }
-        off += c;
-        if (v < w) {
-            comp_add(sh, sl, part(v, 1));
-            sl += part(v, 2);
-        }
-    }
-    S.N_i = off;
-    int s0, s1;
-    segment(P.N, w, s0, s1);
-    int jl = 0;
-    uint32_t bits = 0u;
-    for (int t = s0; t < s1; ++t) {
-        const float r = get_r(t);
-        const bool v = r == r;
         if (v) {
             comp_add(sh, sl, r);
             put_s(s0 + jl, sh + sl);
@@ -382,6 +343,31 @@ __host__ __device__ __forceinline__ void phase6_prefix(const SegParams& P, int w
             bits = 0u;
         }
     }
+    part(w, 0) = (float)jl;
+    part(w, 1) = sh;
+    part(w, 2) = sl;
+}
+
+// ---- phase 6: segment offsets ---------------------------------------------------------
+template <int KH, class Part>
+__host__ __device__ __forceinline__ void phase6_offsets(int w, Lane<KH>& S, Part part) {
+    int off = 0;
+    float sh = 0.f, sl = 0.f;
+#pragma unroll
+    for (int v = 0; v < kNW; ++v) {
+        const int c = (int)part(v, 0);
+        S.cnt_off[v] = off;
+        S.sum_off_hi[v] = sh;
+        S.sum_off_lo[v] = sl;
+        if (v == w) {
+            S.mycnt = c;
+            S.myoff = off;
+        }
+        off += c;
+        comp_add(sh, sl, part(v, 1));
+        sl += part(v, 2);
+    }
+    S.N_i = off;
 }
 
 // Date slot (offset from the segment start) of the n-th (0-based) valid date
@@ -419,6 +405,13 @@ __host__ __device__ __forceinline__ void phase7_mosum(const SegParams& P, int w,
     segment(P.N, w, s0, s1);
     const int n_i = S.n_i, h = S.h;
     const int mycnt = S.mycnt, off = S.myoff;
+    float myoh = 0.f, myol = 0.f;
+#pragma unroll
+    for (int u = 0; u < kNW; ++u)
+        if (u == w) {
+            myoh = S.sum_off_hi[u];
+            myol = S.sum_off_lo[u];
+        }
     int first = -1;
     float mh = 0.f, ml = 0.f;
     for (int jl = jlo; jl < jhi; ++jl) {
@@ -427,16 +420,20 @@ __host__ __device__ __forceinline__ void phase7_mosum(const SegParams& P, int w,
             const float sj = get_s(s0 + jl);
             const int g = J - h;  // >= 1 because J > n_i >= h
             int v = 0, offv = 0;  // segment holding valid position g (select chain, no indexing)
+            float oh = 0.f, ol = 0.f;
 #pragma unroll
             for (int u = 1; u < kNW; ++u)
                 if (S.cnt_off[u] < g) {
                     v = u;
                     offv = S.cnt_off[u];
+                    oh = S.sum_off_hi[u];
+                    ol = S.sum_off_lo[u];
                 }
             int g0, g1;
             segment(P.N, v, g0, g1);
             const float sg = get_s(g0 + (g - offv - 1));
-            const float W = sj - sg;
+            // S_J - S_g with both prefix sums split into segment offset + local sum
+            const float W = (sj - sg) + ((myoh - oh) + (myol - ol));
             float th = S.thr;
             if (J > S.jlim) th = S.thr * sqrtf(logf((float)J / (float)n_i));
             if (first < 0 && fabsf(W) > th) first = jl;
