@@ -36,6 +36,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "BFAST-monitor pixels/s at 8.4M px x 414 dates; p50/p99 tile latency"
+# DRAM bytes per pixel per launch from the ncu captures summarised in
+# profiles/ (None once the kernel changes after the capture).
+TRAFFIC_PER_PX = {"f32": (1.786e9 / 1048576,), "i16": (None,)}
+
 WORKLOAD = "c2: full scene 8,388,608 px x 414 dates, n_hist=228, K=8, f=23, h=0.25, plain float32"
 
 
@@ -174,67 +178,89 @@ def run_ours(args):
     w = synth.workload_torch(name, device=dev, dtype="f32", m=args.pixels)
     m, N, n_hist, K = w["m"], w["N"], w["n_hist"], 8
     Y = w["Y"]
-    form = args.form
-    if form == "i16":
-        Y = torch.where(torch.isnan(Y), torch.full_like(Y, -32768.0),
-                        torch.clamp(torch.round(Y * 1e4), -32767, 32767)).to(torch.int16)
-    dtype_code = bfm.BFM_F32 if form == "f32" else bfm.BFM_I16
-    algo = bfm.BFM_ALGO_SIMT
     design = bfm.Design(w["dates"], 3, 23.0)
     out = bfm.empty_outputs(K, m, dev)
     stream = torch.cuda.current_stream(dev)
-
-    def step():
-        bfm.bfm_monitor_ex(design, Y, dtype_code, None, m, n_hist, w["h_frac"], w["lam"], out["break_idx"],
-                           out["mean_mosum"], out["sigma"], out["beta"], out["status"], algo, stream)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    if bfm.bfm_device_errors(stream) != 0:
-        raise RuntimeError("device error word set during warm-up")
-    clocks = Clocks(local)
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.2)
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    evs[0].record(stream)
-    for i in range(args.steps):
-        step()
-        evs[i + 1].record(stream)
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    clk = clocks.stop()
-    per = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
-    total_ms = evs[0].elapsed_time(evs[-1])
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * m * args.steps / (total_ms / 1e3)
-    ms_step = total_ms / args.steps
-    elt = 4 if form == "f32" else 2
-    alg_bytes = N * m * elt + m * (4 + 4 + 4 + 4 * K + 1)
     hbm, peak_kind = _peaks()
-    achieved = alg_bytes / (statistics.mean(per) / 1e3) / 1e9
 
-    # ---- end to end through the host-buffer entry point ------------------------------
+    def time_form(form):
+        """Device-resident timing of one form: W warm-up calls, then K calls
+        bracketed by CUDA events on the launching stream."""
+        if form == "f32":
+            Yf, dt, algo = Y, bfm.BFM_F32, bfm.BFM_ALGO_SIMT
+        else:
+            Yf = torch.where(torch.isnan(Y), torch.full_like(Y, -32768.0),
+                             torch.clamp(torch.round(Y * 1e4), -32767, 32767)).to(torch.int16)
+            dt, algo = bfm.BFM_I16, bfm.BFM_ALGO_MMA
+
+        def step():
+            bfm.bfm_monitor_ex(design, Yf, dt, None, m, n_hist, w["h_frac"], w["lam"], out["break_idx"],
+                               out["mean_mosum"], out["sigma"], out["beta"], out["status"], algo, stream)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        if bfm.bfm_device_errors(stream) != 0:
+            raise RuntimeError("device error word set during warm-up")
+        clocks = Clocks(local)
+        if ws > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        time.sleep(0.2)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+        evs[0].record(stream)
+        for i in range(args.steps):
+            step()
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
+        clk = clocks.stop()
+        per = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+        total_ms = evs[0].elapsed_time(evs[-1])
+        if ws > 1:
+            t = torch.tensor([total_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        elt = 4 if form == "f32" else 2
+        alg_bytes = N * m * elt + m * (4 + 4 + 4 + 4 * K + 1)
+        achieved = alg_bytes / (statistics.mean(per) / 1e3) / 1e9
+        srt = sorted(per)
+        del Yf
+        return {"value": ws * m * args.steps / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
+                "latency_ms": {"p50": srt[len(srt) // 2],
+                               "p99": srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)],
+                               "unit": "one full-scene call"},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                             "frac": achieved / hbm, "traffic": TRAFFIC_PER_PX.get(form, (None,))[0] and
+                             TRAFFIC_PER_PX[form][0] * m, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+                             "algorithmic_bytes_per_launch": alg_bytes},
+                "clocks": clk, "dtype": "f32" if form == "f32" else "i16",
+                "algo": "simt" if form == "f32" else "tcgen05"}
+
+    forms = [f.strip() for f in args.forms.split(",") if f.strip()]
+    res = {f: time_form(f) for f in forms}
+    form = forms[0]
+    main = res[form]
+    value, ms_step = main["value"], main["ms_per_step"]
+    elt = 4 if form == "f32" else 2
+
+    # ---- end to end (float32 scene through bfm_monitor_host) through the host-buffer entry point ------------------------------
     e2e = None
     if not args.no_e2e:
         Yh = torch.empty(Y.shape, dtype=Y.dtype, pin_memory=True)
         Yh.copy_(Y)
+        e_dt, e_elt = bfm.BFM_F32, 4
         oh = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()}
         chunk = 1 << 20
-        wsb = bfm.bfm_monitor_host_workspace(design, dtype_code, chunk, False)
+        wsb = bfm.bfm_monitor_host_workspace(design, e_dt, chunk, False)
         wbuf = torch.empty(wsb, dtype=torch.uint8, device=dev)
         del Y
         torch.cuda.empty_cache()
 
         def hstep():
-            bfm.bfm_monitor_host(design, Yh, dtype_code, None, m, n_hist, w["h_frac"], w["lam"], oh["break_idx"],
+            bfm.bfm_monitor_host(design, Yh, e_dt, None, m, n_hist, w["h_frac"], w["lam"], oh["break_idx"],
                                  oh["mean_mosum"], oh["sigma"], oh["beta"], oh["status"], wbuf, wsb, chunk, stream)
 
         hstep()
@@ -252,7 +278,7 @@ def run_ours(args):
             t = torch.tensor([e_ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e_ms = float(t.item())
-        e2e = {"value": ws * m / (e_ms / 1e3), "unit": "pixels/s", "h2d_bytes_per_step": N * m * elt,
+        e2e = {"value": ws * m / (e_ms / 1e3), "unit": "pixels/s", "h2d_bytes_per_step": N * m * e_elt,
                "d2h_bytes_per_step": m * (4 + 4 + 4 + 4 * K + 1), "ms_per_step": e_ms,
                "api": "bfm_monitor_host (pinned host Y and outputs, 1 Mi-pixel chunks)"}
         Ysrc = Yh
@@ -265,22 +291,18 @@ def run_ours(args):
         cpu = {"value": rate, "unit": "pixels/s", "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count())),
                "kind": "oracle", "sample": f"first {n} pixels of the same scene, all {N} dates, FP64 oracle ({dt:.1f} s)"}
 
-    srt = sorted(per)
     line = {
         "metric": METRIC, "value": value, "unit": "pixels/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if form == "f32" else "i16", "data": "synthetic",
+        "vs_baseline": None, "dtype": main["dtype"], "data": "synthetic",
         "config": {"workload": (WORKLOAD if form == "f32" else WORKLOAD.replace("plain float32", "int16 storage"))
                    if args.pixels is None else f"c2 recipe with {m} pixels (profiling case)",
-                   "pixels": m, "dates": N, "n_hist": n_hist, "K": K, "form": form,
-                   "algo": "simt", "l2": "inputs larger than L2 (Y is %.1f GB per step)" % (N * m * elt / 1e9),
+                   "pixels": m, "dates": N, "n_hist": n_hist, "K": K, "form": form, "algo": main["algo"],
+                   "l2": "inputs larger than L2 (Y is %.1f GB per step)" % (N * m * elt / 1e9),
                    "parallelism": f"{ws} independent scene(s), one per GPU"},
-        "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)],
-                       "unit": "one full-scene call"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                     "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
-                     "algorithmic_bytes_per_launch": alg_bytes},
-        "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": args.steps,
+        "latency_ms": main["latency_ms"], "roofline": main["roofline"],
+        "cpu_baseline": cpu, "e2e": e2e, "clocks": main["clocks"], "gpu_launches": args.steps,
+        "forms": {f: {k: v for k, v in r.items() if k != "clocks"} for f, r in res.items()},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -295,7 +317,9 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="f32", choices=["f32", "i16"])
+    ap.add_argument("--forms", default="f32,i16",
+                    help="comma list; the first is the headline (f32 = plain CUDA-core form, "
+                         "i16 = int16 storage on tensor cores)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--pixels", type=int, default=None,
                     help="fewer pixels of the same recipe (profiling captures only; not a bench line)")

@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "bfm_internal.cuh"
 
 namespace bfm {
@@ -28,30 +30,47 @@ uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull) 
     return h;
 }
 
-// Fill the per-date basis rows (layout of bfm::Basis) in double, store float.
-void fill_basis(const bfm_design_s& d, std::vector<float>& rows) {
+// Per-date basis rows (layout of bfm::Basis) in double.
+void basis_rows(const bfm_design_s& d, std::vector<double>& rows) {
     const int k = d.k, K = d.K, NB = d.NB;
     auto S = [&](int j) { return j <= k ? 2 + 2 * (j - 1) : K + 1 + 2 * (j - k - 1); };
     auto TS = [&](int j) { return K + 1 + 2 * k + 2 * (j - 1); };
-    rows.assign((size_t)d.N * NB, 0.0f);
+    rows.assign((size_t)d.N * NB, 0.0);
     const double two_pi = 6.283185307179586476925286766559;
     for (int t = 0; t < d.N; ++t) {
-        float* r = rows.data() + (size_t)t * NB;
+        double* r = rows.data() + (size_t)t * NB;
         const double tp = (d.dates[t] - d.c) / d.s;
-        r[0] = 1.0f;
-        r[1] = (float)tp;
-        r[K] = (float)(tp * tp);
+        r[0] = 1.0;
+        r[1] = tp;
+        r[K] = tp * tp;
         for (int j = 1; j <= 2 * k; ++j) {
             const double a = two_pi * (double)j * d.dates[t] / d.f;
             const double sj = std::sin(a), cj = std::cos(a);
-            r[S(j)] = (float)sj;
-            r[S(j) + 1] = (float)cj;
+            r[S(j)] = sj;
+            r[S(j) + 1] = cj;
             if (j <= k) {
-                r[TS(j)] = (float)(tp * sj);
-                r[TS(j) + 1] = (float)(tp * cj);
+                r[TS(j)] = tp * sj;
+                r[TS(j) + 1] = tp * cj;
             }
         }
     }
+}
+
+// Tensor-core B table: basis value (row r, date t) split as fp16 hi + lo, at
+// byte (t/8)*512 + (r/8)*128 + (r%8)*16 + (t%8)*2 of each table.
+void tc_tables(const bfm_design_s& d, const std::vector<double>& rows, int npad, std::vector<unsigned char>& out) {
+    const size_t one = (size_t)(npad / 8) * 512;
+    out.assign(2 * one, 0);
+    const int nbr = 3 + 6 * d.k;
+    for (int t = 0; t < d.N; ++t)
+        for (int r = 0; r < nbr; ++r) {
+            const double v = rows[(size_t)t * d.NB + r];
+            const __half hi = __double2half(v);
+            const __half lo = __double2half(v - (double)__half2float(hi));
+            const size_t o = (size_t)(t / 8) * 512 + (size_t)(r / 8) * 128 + (size_t)(r % 8) * 16 + (size_t)(t % 8) * 2;
+            std::memcpy(out.data() + o, &hi, 2);
+            std::memcpy(out.data() + one + o, &lo, 2);
+        }
 }
 
 bool valid_common(bfm_design_t d, int dtype, int64_t m, int n_hist, double h_frac, double lambda, const char* fn) {
@@ -227,18 +246,28 @@ bfm_status bfm_design_create(const double* dates, int N, int k_harm, double f, b
     d->device = dev;
     d->key = key;
     d->refcount = 1;
-    std::vector<float> rows;
-    fill_basis(*d, rows);
+    std::vector<double> rowsd;
+    basis_rows(*d, rowsd);
+    std::vector<float> rows(rowsd.begin(), rowsd.end());
     e = cudaMalloc(&d->d_basis, rows.size() * sizeof(float));
     if (e != cudaSuccess) {
         delete d;
         return cuda_fail(e, "bfm_design_create: cudaMalloc");
     }
     e = cudaMemcpy(d->d_basis, rows.data(), rows.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && N <= kTcMaxDates) {
+        const int npad = (N + 31) / 32 * 32;  // whole 32-date chunks
+        std::vector<unsigned char> tab;
+        tc_tables(*d, rowsd, npad, tab);
+        e = cudaMalloc(&d->d_phi_tc, tab.size());
+        if (e == cudaSuccess) e = cudaMemcpy(d->d_phi_tc, tab.data(), tab.size(), cudaMemcpyHostToDevice);
+        d->npad_tc = npad;
+    }
     if (e != cudaSuccess) {
         cudaFree(d->d_basis);
+        if (d->d_phi_tc) cudaFree(d->d_phi_tc);
         delete d;
-        return cuda_fail(e, "bfm_design_create: cudaMemcpy");
+        return cuda_fail(e, "bfm_design_create: device tables");
     }
     g_cache.push_back(d);
     *out = d;
@@ -259,6 +288,7 @@ bfm_status bfm_design_destroy(bfm_design_t d) {
                 cudaGetDevice(&cur);
                 if (cur != d->device) cudaSetDevice(d->device);
                 cudaFree(d->d_basis);
+                if (d->d_phi_tc) cudaFree(d->d_phi_tc);
                 if (cur != d->device) cudaSetDevice(cur);
                 delete d;
             }
@@ -292,14 +322,19 @@ bfm_status bfm_monitor_ex(bfm_design_t d, const void* Y, int dtype, const uint32
         set_error("bfm_monitor: the design belongs to another device");
         return BFM_EINVAL;
     }
-    if (algo == BFM_ALGO_MMA) {
-        set_error("bfm_monitor: the tensor-core form is not available in this build");
-        return BFM_EUNSUPPORTED;
-    }
-    if (algo != BFM_ALGO_AUTO && algo != BFM_ALGO_SIMT) {
+    if (algo != BFM_ALGO_AUTO && algo != BFM_ALGO_SIMT && algo != BFM_ALGO_MMA) {
         set_error("bfm_monitor: unknown algo");
         return BFM_EINVAL;
     }
+    const bool mma_ok = mma_supported(d, dtype, n_hist, h_frac, nullptr);
+    if (algo == BFM_ALGO_MMA && !mma_ok) {
+        set_error("bfm_monitor: the tensor-core form needs int16 storage, N <= 448 and a bandwidth of at most 95 "
+                  "observations");
+        return BFM_EUNSUPPORTED;
+    }
+    if (algo == BFM_ALGO_MMA || (algo == BFM_ALGO_AUTO && mma_ok))
+        return launch_mma(d, Y, mask_bits, m, n_hist, h_frac, lambda, break_idx, mean_mosum, sigma, beta, status,
+                          (cudaStream_t)stream);
     return launch_simt(d, Y, dtype, mask_bits, m, n_hist, h_frac, lambda, break_idx, mean_mosum, sigma, beta, status,
                        (cudaStream_t)stream);
 }
@@ -409,9 +444,11 @@ bfm_status bfm_device_errors(void* stream, uint32_t* bits) {
         set_error("bfm_device_errors: bits is NULL");
         return BFM_EINVAL;
     }
-    unsigned int v = 0;
+    unsigned int v = 0, v2 = 0;
     cudaError_t e = simt_read_clear_errors((cudaStream_t)stream, &v);
+    if (e == cudaSuccess) e = mma_read_clear_errors((cudaStream_t)stream, &v2);
     if (e != cudaSuccess) return cuda_fail(e, "bfm_device_errors");
+    v |= v2;
     *bits = v;
     return BFM_OK;
 }

@@ -1,0 +1,134 @@
+"""Tensor-core (tcgen05) form vs the FP64 oracle, element by element.
+
+int16 storage, Gram / X'My / fitted values on fp16 tensor cores with split
+hi/lo operands and FP32 accumulation, FP32 solve with one refinement step.
+Tolerance of this form: 1e-4 (beta column-scaled, sigma relative, mean MOSUM
+relative to max(1, |ref|)); break indices equal except margin-tied pixels.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from _parity import compare, to_numpy
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_MMA = 1e-4
+ALGO_MMA = 2
+
+
+@pytest.fixture(scope="module")
+def bfm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1807_01751_gb300 as bfm
+    bfm.load()
+    return bfm
+
+
+def _run(bfm, dates, Y, *, k, n_hist, h_frac, lam, mask=None, algo=ALGO_MMA):
+    d = bfm.Design(dates, k, 23.0)
+    Yd = torch.from_numpy(np.ascontiguousarray(Y)).cuda()
+    md = None if mask is None else torch.from_numpy(mask.view(np.int32)).cuda()
+    out = bfm.monitor(d, Yd, n_hist=n_hist, h_frac=h_frac, lam=lam, mask_bits=md, algo=algo)
+    torch.cuda.synchronize()
+    assert bfm.bfm_device_errors() == 0
+    return to_numpy(out)
+
+
+def _check(dates, Y, gpu, *, k, n_hist, h_frac, lam, mask=None, tol=TOL_MMA):
+    ref = oracle.monitor(dates, Y, k=k, f=23.0, n_hist=n_hist, h_frac=h_frac, lam=lam, mask_bits=mask)
+    rep = compare(gpu, ref, dates, k, 23.0, tol=tol)
+    print(rep)
+    assert rep["ok"], rep
+    return rep, ref
+
+
+def test_c3_mma(bfm):
+    """c3: the c1 scene in int16 (NDVI*1e4, -32768 missing), 32 tiles of 128."""
+    w = synth.workload("c3")
+    g = _run(bfm, w["dates"], w["Y"], k=3, n_hist=w["n_hist"], h_frac=w["h_frac"], lam=w["lam"])
+    rep, _ = _check(w["dates"], w["Y"], g, k=3, n_hist=w["n_hist"], h_frac=w["h_frac"], lam=w["lam"])
+    assert rep["beta_err_max"] < 1e-5 and rep["mean_err_max"] < 2e-5
+
+
+def test_c2_recipe_int16(bfm):
+    """c2 recipe (N = 414, n_hist = 228, ~60 % Markov clouds), int16, 8192 px."""
+    w = synth.workload("c2", m=8192, dtype="i16")
+    g = _run(bfm, w["dates"], w["Y"], k=3, n_hist=w["n_hist"], h_frac=w["h_frac"], lam=w["lam"])
+    _check(w["dates"], w["Y"], g, k=3, n_hist=w["n_hist"], h_frac=w["h_frac"], lam=w["lam"])
+
+
+@pytest.mark.parametrize("m", [1, 100, 129, 1000, 4093, 4104])
+def test_ragged(bfm, m):
+    """m < 128, m % 8 != 0 (plain loader) and m % 8 == 0 with a ragged last
+    tile (TMA loader, zero-filled columns)."""
+    w = synth.workload("c3", m=m)
+    g = _run(bfm, w["dates"], w["Y"], k=3, n_hist=w["n_hist"], h_frac=w["h_frac"], lam=w["lam"])
+    _check(w["dates"], w["Y"], g, k=3, n_hist=w["n_hist"], h_frac=w["h_frac"], lam=w["lam"])
+
+
+def test_mask_bits(bfm):
+    w = synth.workload("c3", m=1024)
+    rng = np.random.default_rng(5)
+    words = 1024 // 32
+    on = rng.random((w["N"], 1024)) > 0.15
+    bits = np.zeros((w["N"], words), np.uint32)
+    for b in range(32):
+        bits |= on[:, b::32].astype(np.uint32) << np.uint32(b)
+    g = _run(bfm, w["dates"], w["Y"], k=3, n_hist=w["n_hist"], h_frac=w["h_frac"], lam=w["lam"], mask=bits)
+    _check(w["dates"], w["Y"], g, k=3, n_hist=w["n_hist"], h_frac=w["h_frac"], lam=w["lam"], mask=bits)
+
+
+@pytest.mark.parametrize("k,N,n_hist", [(1, 150, 70), (2, 300, 180), (3, 448, 300)])
+def test_harmonics_and_lengths(bfm, k, N, n_hist):
+    d, Y, _ = synth.scene(seed=40 + k, m=2048, N=N, n_hist=n_hist, f=23.0, k_gen=k, intercept=0.45,
+                          slope=0.0002, coef_umax=0.25, noise_sd=0.03, miss="markov", p_a=0.25, p_b=0.3,
+                          break_frac=0.2, step=(-0.4, -0.1), dtype="i16")
+    g = _run(bfm, d, Y, k=k, n_hist=n_hist, h_frac=0.25, lam=1.75)
+    _check(d, Y, g, k=k, n_hist=n_hist, h_frac=0.25, lam=1.75)
+
+
+def test_edge_statuses(bfm):
+    w = synth.workload("c3", m=256)
+    Y = w["Y"].copy()
+    N, n = w["N"], w["n_hist"]
+    Y[:, 0] = -32768
+    Y[8:n, 127] = -32768
+    Y[n:, 128] = -32768
+    X = oracle.design(w["dates"], 3, 23.0)
+    Y[:, 255] = np.round(X @ np.array([5000, 10, 2000, 0, 0, 500, 0, 0])).astype(np.int16)
+    g = _run(bfm, w["dates"], Y, k=3, n_hist=n, h_frac=0.25, lam=w["lam"])
+    rep, ref = _check(w["dates"], Y, g, k=3, n_hist=n, h_frac=0.25, lam=w["lam"])
+    assert list(ref["status"][[0, 127, 128]]) == [1, 1, 4]
+
+
+def test_mma_matches_simt_on_same_input(bfm):
+    """Both forms on the same int16 input agree within the precision form's tolerance."""
+    w = synth.workload("c2", m=4096, dtype="i16")
+    kw = dict(k=3, n_hist=w["n_hist"], h_frac=w["h_frac"], lam=w["lam"])
+    a = _run(bfm, w["dates"], w["Y"], algo=ALGO_MMA, **kw)
+    b = _run(bfm, w["dates"], w["Y"], algo=1, **kw)
+    ok = (a["status"] == 0) & (b["status"] == 0)
+    assert (a["status"] == b["status"]).all()
+    rel = np.abs(a["sigma"][ok] - b["sigma"][ok]) / b["sigma"][ok]
+    assert rel.max() < 1e-4
+
+
+def test_c2_full_int16_sampled(bfm):
+    """The full c2 scene stored as int16, in the benchmark's launch
+    configuration; the oracle checks a seeded sample of pixels."""
+    w = synth.workload_torch("c2", device="cuda", dtype="i16")
+    d = bfm.Design(w["dates"], 3, 23.0)
+    out = bfm.monitor(d, w["Y"], n_hist=w["n_hist"], h_frac=w["h_frac"], lam=w["lam"], algo=ALGO_MMA)
+    torch.cuda.synchronize()
+    assert bfm.bfm_device_errors() == 0
+    m = w["m"]
+    rng = np.random.default_rng(1)
+    idx = np.unique(np.concatenate([np.arange(128), np.arange(m - 128, m), rng.choice(m, 3840, replace=False)]))
+    it = torch.from_numpy(idx).cuda()
+    Ys = w["Y"].index_select(1, it).cpu().numpy()
+    res = {k: (v.index_select(1, it) if v.dim() == 2 else v.index_select(0, it)).cpu().numpy() for k, v in out.items()}
+    _check(w["dates"], Ys, res, k=3, n_hist=w["n_hist"], h_frac=w["h_frac"], lam=w["lam"])
