@@ -14,11 +14,11 @@
 //            double-buffered against the next chunk's operand writes
 //   solve    every thread: Gram from the basis sums, Cholesky, beta0 (FP32)
 //   yhat0    TMEM[Y] = [beta_hi | beta_lo] x Phi (Phi read MN-major: rows =
-//            coefficients, columns = dates) over the history dates
+//            coefficients, columns = dates) over all dates
 //   refine   r0 = y - yhat0 on valid history dates, split fp16 hi/lo, then
 //            TMEM[c] += r0 x Phi: one refinement step beta = beta0 + G^-1 c;
 //            sum r^2 = sum r0^2 - delta'c (sigma-hat, Algorithm 1 step 5)
-//   yhat     TMEM[Y] = beta x Phi over all dates
+//   yhat     TMEM[Y] += [delta_hi | delta_lo] x Phi (yhat = yhat0 + X delta)
 //   MOSUM    per thread, date by date: r = y - yhat, valid residuals in a
 //            ring of h+1, the window sum of h valid residuals (Eq. 3) kept
 //            compensated, first crossing of lambda*sqrt(log+(j/n)) (Eq. 4)
@@ -106,10 +106,12 @@ __device__ __forceinline__ void mma_kblock(uint32_t dcol, const unsigned char* a
     ptx::mma_f16(dcol, ad, bd, ptx::idesc_f16(kTile, n, false), acc);
 }
 
-// yhat over dates [0, ncols) into TMEM column base dcol: A = [b_hi | 0], [b_lo | 0]
-// (K = 16 coefficient slots), B = Phi rows 0..15 read MN-major (N = dates).
+// X b over dates [0, ncols) into TMEM column base dcol (added to what is there
+// when `accumulate`): A = [b_hi | 0], [b_lo | 0] (K = 16 coefficient slots),
+// B = Phi rows 0..15 read MN-major (N = dates).
 __device__ __forceinline__ void mma_yhat(uint32_t dcol, const unsigned char* bhi, const unsigned char* blo,
-                                         const unsigned char* phi_hi, const unsigned char* phi_lo, int ncols) {
+                                         const unsigned char* phi_hi, const unsigned char* phi_lo, int ncols,
+                                         bool accumulate) {
     const uint64_t ah = ptx::smem_desc(bhi, kALbo, 128), al = ptx::smem_desc(blo, kALbo, 128);
     for (int n0 = 0; n0 < ncols; n0 += 256) {
         const int n = ncols - n0 < 256 ? ncols - n0 : 256;
@@ -117,7 +119,7 @@ __device__ __forceinline__ void mma_yhat(uint32_t dcol, const unsigned char* bhi
         // MN-major B: K-direction (coefficient) core stride 128 B, N-direction (date) stride 512 B
         const uint64_t bh = ptx::smem_desc(phi_hi + (size_t)(n0 / 8) * kPhiLbo, kPhiSbo, kPhiLbo);
         const uint64_t bl = ptx::smem_desc(phi_lo + (size_t)(n0 / 8) * kPhiLbo, kPhiSbo, kPhiLbo);
-        ptx::mma_f16(dcol + (uint32_t)n0, ah, bh, id, false);
+        ptx::mma_f16(dcol + (uint32_t)n0, ah, bh, id, accumulate);
         ptx::mma_f16(dcol + (uint32_t)n0, al, bh, id, true);
         ptx::mma_f16(dcol + (uint32_t)n0, ah, bl, id, true);
     }
@@ -275,12 +277,12 @@ __global__ void __launch_bounds__(kTile) mma_kernel(const __grid_constant__ CUte
     const bool nonsingular = cholesky<K>(G, L, dinv);
     chol_solve<K>(L, dinv, bb, beta);
 
-    // beta/16 as fp16 hi and lo A rows (coefficient slots 0..K-1, 8..15 zero) in buffer 0
-    auto write_beta = [&]() {
+    // coef/16 as fp16 hi and lo A rows (coefficient slots 0..K-1, 8..15 zero) in buffer 0
+    auto write_beta = [&](const float (&coef)[K]) {
         float h[8], l[8], z[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const float b16 = i < K ? beta[i] * 0.0625f : 0.f;
+            const float b16 = i < K ? coef[i] * 0.0625f : 0.f;
             h[i] = __half2float(__float2half_rn(b16));
             l[i] = b16 - h[i];
             z[i] = 0.f;
@@ -294,11 +296,11 @@ __global__ void __launch_bounds__(kTile) mma_kernel(const __grid_constant__ CUte
         __syncthreads();
     };
 
-    // ---- yhat0 over the history ----------------------------------------------------------
-    write_beta();
+    // ---- yhat0 = X beta0 over all dates ------------------------------------------------------
+    write_beta(beta);
     if (tid == 0) {
         ptx::tc_fence_after();
-        mma_yhat(tmem + kColY, sA, sA + kPlane, phi_hi, phi_lo, P.nhp);
+        mma_yhat(tmem + kColY, sA, sA + kPlane, phi_hi, phi_lo, P.npad, false);
         ptx::mma_commit(bar_done);
     }
     ok &= wait_done();
@@ -349,8 +351,9 @@ __global__ void __launch_bounds__(kTile) mma_kernel(const __grid_constant__ CUte
     ok &= wait_done();
     float sigma, scale, thr;
     int h, jlim;
+    float dl[K];
     {
-        float v16[16], cc[K], dl[K];
+        float v16[16], cc[K];
         ptx::tmem_ld16(tmem + lane_base + kColC, v16);
 #pragma unroll
         for (int i = 0; i < K; ++i) cc[i] = 4.f * v16[i];
@@ -370,11 +373,14 @@ __global__ void __launch_bounds__(kTile) mma_kernel(const __grid_constant__ CUte
         jlim = (int)floor(kEuler * (double)n_i);
     }
 
-    // ---- yhat over all dates ------------------------------------------------------------------
-    write_beta();
+    // ---- yhat = yhat0 + X delta over all dates ---------------------------------------------------
+    // Adding the correction to the stored yhat0 (rather than forming X beta
+    // again) makes the fp16 split error of beta0 -- which lies in the span of
+    // X -- cancel between the refinement residuals and the final residuals.
+    write_beta(dl);
     if (tid == 0) {
         ptx::tc_fence_after();
-        mma_yhat(tmem + kColY, sA, sA + kPlane, phi_hi, phi_lo, P.npad);
+        mma_yhat(tmem + kColY, sA, sA + kPlane, phi_hi, phi_lo, P.npad, true);
         ptx::mma_commit(bar_done);
     }
     ok &= wait_done();
