@@ -240,7 +240,10 @@ bfm_status dispatch_dtype(int dtype, bool tma, const CUtensorMap& tm, const Moni
 size_t simt_smem_bytes(int N, int k, int dtype, int* box_rows, int* nbox) {
     const int elt = dtype == BFM_F32 ? 4 : 2;
     const int nb = (N + 255) / 256;
-    const int br = (N + nb - 1) / nb;
+    int br = (N + nb - 1) / nb;
+    // every TMA box must start on a 128-byte boundary of shared memory: with
+    // 64-byte int16 rows the box height has to be even
+    if ((br * 32 * elt) % 128 != 0) ++br;
     const int rows = nb * br;
     const size_t tile = ((size_t)rows * 32 * elt + 127) & ~(size_t)127;
     const size_t work = dtype == BFM_F32 ? 0 : (((size_t)N * 32 * 4 + 127) & ~(size_t)127);
