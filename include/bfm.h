@@ -170,6 +170,45 @@ bfm_status bfm_monitor_host(bfm_design_t d, const void *Y_host, int dtype, const
                             float *mean_mosum, float *sigma, float *beta, uint8_t *status, void *workspace,
                             size_t workspace_bytes, int64_t chunk_px, void *stream);
 
+/*
+ * Batched persistent launch -- many scene tiles of uneven pixel counts,
+ * series lengths (their own designs), harmonics and storage types processed
+ * by ONE kernel launch replayed from a CUDA graph.  The paper processes one
+ * scene per call (Algorithm 2); batching is a serving extension with the same
+ * per-pixel results: every pixel's outputs equal those of bfm_monitor with
+ * BFM_ALGO_SIMT on its tile alone.
+ *   bfm_batch_create    new empty batch on the current device (owned by the
+ *                       caller, freed by bfm_batch_destroy).
+ *   bfm_batch_add       appends one tile; arguments and errors as
+ *                       bfm_monitor (device buffers, caller-owned and kept
+ *                       alive while the batch runs).  *tile_id (nullable)
+ *                       receives its index.  The batch holds a reference to
+ *                       the design.
+ *   bfm_batch_run       enqueues the whole batch on `stream`: a graph of a
+ *                       work-counter reset and the persistent kernel (CTAs =
+ *                       SM count x CTAs per SM, taking `grab` 32-pixel blocks
+ *                       at a time).  The first run after adds uploads the tile
+ *                       table and instantiates the graph; later runs replay it.
+ *   bfm_batch_autotune  times every (CTAs per SM, grab in {1,2,4,8})
+ *                       candidate on this batch (3 replays each, CUDA events on
+ *                       `stream`, synchronising) and keeps the fastest; results
+ *                       are cached per batch signature (N, K, dtype and pixel
+ *                       count class of every tile) for later batches.  Outputs
+ *                       (nullable): the chosen pair and its time in ms.
+ *   bfm_batch_set_config  fixes the pair by hand (ctas_per_sm 0 = automatic).
+ * The library allocates the device tile table and work counter.
+ */
+typedef struct bfm_batch_s *bfm_batch_t;
+bfm_status bfm_batch_create(bfm_batch_t *out);
+bfm_status bfm_batch_add(bfm_batch_t b, bfm_design_t d, const void *Y, int dtype, const uint32_t *mask_bits,
+                         int64_t m, int n_hist, double h_frac, double lambda, int32_t *break_idx, float *mean_mosum,
+                         float *sigma, float *beta, uint8_t *status, int *tile_id);
+bfm_status bfm_batch_run(bfm_batch_t b, void *stream);
+bfm_status bfm_batch_autotune(bfm_batch_t b, void *stream, int *ctas_per_sm, int *grab, float *best_ms);
+bfm_status bfm_batch_set_config(bfm_batch_t b, int ctas_per_sm, int grab);
+int bfm_batch_tiles(bfm_batch_t b);
+bfm_status bfm_batch_destroy(bfm_batch_t b);
+
 /* Reads and clears the library's device error word (bit 0: a tile load wait
  * gave up).  Synchronises `stream`. */
 bfm_status bfm_device_errors(void *stream, uint32_t *bits);

@@ -75,6 +75,22 @@ def load(build_if_missing: bool = True):
         lib.bfm_monitor_host.restype = i32
         lib.bfm_device_errors.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
         lib.bfm_device_errors.restype = i32
+        lib.bfm_batch_create.argtypes = [ctypes.POINTER(vp)]
+        lib.bfm_batch_create.restype = i32
+        lib.bfm_batch_add.argtypes = [vp, vp, vp, i32, vp, i64, i32, dbl, dbl, vp, vp, vp, vp, vp,
+                                      ctypes.POINTER(i32)]
+        lib.bfm_batch_add.restype = i32
+        lib.bfm_batch_run.argtypes = [vp, vp]
+        lib.bfm_batch_run.restype = i32
+        lib.bfm_batch_autotune.argtypes = [vp, vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                           ctypes.POINTER(ctypes.c_float)]
+        lib.bfm_batch_autotune.restype = i32
+        lib.bfm_batch_set_config.argtypes = [vp, i32, i32]
+        lib.bfm_batch_set_config.restype = i32
+        lib.bfm_batch_tiles.argtypes = [vp]
+        lib.bfm_batch_tiles.restype = i32
+        lib.bfm_batch_destroy.argtypes = [vp]
+        lib.bfm_batch_destroy.restype = i32
         _lib = lib
         return lib
 
@@ -167,6 +183,40 @@ def bfm_device_errors(stream=None) -> int:
     return v.value
 
 
+def bfm_batch_create() -> int:
+    h = ctypes.c_void_p()
+    _check(load().bfm_batch_create(ctypes.byref(h)))
+    return h.value
+
+
+def bfm_batch_add(batch, design, Y, dtype, mask_bits, m, n_hist, h_frac, lam, break_idx, mean_mosum, sigma, beta,
+                  status) -> int:
+    tid = ctypes.c_int(-1)
+    _check(load().bfm_batch_add(int(batch), int(design), _ptr(Y), int(dtype), _ptr(mask_bits), int(m), int(n_hist),
+                                float(h_frac), float(lam), _ptr(break_idx), _ptr(mean_mosum), _ptr(sigma),
+                                _ptr(beta), _ptr(status), ctypes.byref(tid)))
+    return tid.value
+
+
+def bfm_batch_run(batch, stream=None):
+    _check(load().bfm_batch_run(int(batch), _stream(stream)))
+
+
+def bfm_batch_autotune(batch, stream=None):
+    c, g, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_float(0)
+    _check(load().bfm_batch_autotune(int(batch), _stream(stream), ctypes.byref(c), ctypes.byref(g),
+                                     ctypes.byref(ms)))
+    return c.value, g.value, ms.value
+
+
+def bfm_batch_set_config(batch, ctas_per_sm: int, grab: int):
+    _check(load().bfm_batch_set_config(int(batch), int(ctas_per_sm), int(grab)))
+
+
+def bfm_batch_destroy(batch):
+    _check(load().bfm_batch_destroy(int(batch)))
+
+
 # ---- convenience layer ----------------------------------------------------------
 
 class Design:
@@ -215,3 +265,43 @@ def monitor(design: Design, Y, *, n_hist: int, h_frac: float, lam: float, mask_b
     bfm_monitor_ex(design, Y, dtype, mask_bits, m, n_hist, h_frac, lam, out["break_idx"], out["mean_mosum"],
                    out["sigma"], out["beta"], out["status"], algo, stream)
     return out
+
+
+class Batch:
+    """Owning wrapper of a bfm_batch_t: tiles added with :meth:`add` run in one
+    persistent launch (:meth:`run`), replayed from a CUDA graph."""
+
+    def __init__(self):
+        self.handle = bfm_batch_create()
+        self.tiles = []
+
+    def add(self, design: Design, Y, *, n_hist: int, h_frac: float, lam: float, mask_bits=None, out=None):
+        import torch
+        dtype = {torch.float32: BFM_F32, torch.int16: BFM_I16}[Y.dtype]
+        m = Y.shape[1]
+        if out is None:
+            out = empty_outputs(design.K, m, Y.device)
+        bfm_batch_add(self.handle, design, Y, dtype, mask_bits, m, n_hist, h_frac, lam, out["break_idx"],
+                      out["mean_mosum"], out["sigma"], out["beta"], out["status"])
+        self.tiles.append((Y, mask_bits, out))  # keep buffers alive
+        return out
+
+    def run(self, stream=None):
+        bfm_batch_run(self.handle, stream)
+
+    def autotune(self, stream=None):
+        return bfm_batch_autotune(self.handle, stream)
+
+    def set_config(self, ctas_per_sm: int, grab: int):
+        bfm_batch_set_config(self.handle, ctas_per_sm, grab)
+
+    def close(self):
+        if self.handle:
+            bfm_batch_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -67,6 +67,13 @@ struct MonitorParams {
     uint8_t* status;
 };
 
+// One tile of a batched launch (device-side descriptor).
+struct BatchTileDesc {
+    MonitorParams P;
+    int64_t block0;  // first 32-pixel work block of this tile
+    int kh, dtype, has_tma, has_mask;
+};
+
 // Each kernel translation unit keeps its own device error word (bit 0: a
 // tile-load wait gave up); these read and clear it, synchronising `s`.
 cudaError_t simt_read_clear_errors(cudaStream_t s, unsigned int* bits);

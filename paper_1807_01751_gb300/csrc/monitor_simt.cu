@@ -42,6 +42,8 @@ cudaError_t simt_read_clear_errors(cudaStream_t s, unsigned int* bits) {
     return e;
 }
 
+bool make_tensor_map(CUtensorMap* tm, const void* Y, int dtype, int64_t m, int N, int box_rows);
+
 namespace {
 
 constexpr uint64_t kLoadWaitLimitNs = 2000000000ull;  // 2 s
@@ -98,45 +100,63 @@ __device__ __forceinline__ void load_x(const float4* __restrict__ B4, int t, flo
     for (int i = 0; i < K; ++i) x[i] = q[i];
 }
 
-template <int KH, typename T, bool kTMA, bool kMask>
-__global__ void __launch_bounds__(kNW * 32) simt_kernel(const __grid_constant__ CUtensorMap tmap, const MonitorParams P) {
-    using B = Basis<KH>;
-    constexpr int K = B::K, NB = B::NB, PS = Partials<KH>::kStride;
-    constexpr bool kInPlace = sizeof(T) == sizeof(float);
+// Shared-memory layout of one 32-pixel tile (see simt_smem_bytes).
+struct TileSmem {
+    unsigned char* tile;
+    float* work;
+    float* part;
+};
 
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    T* tile = reinterpret_cast<T*>(smem_raw);
+template <int KH, typename T>
+__device__ __forceinline__ TileSmem tile_smem(unsigned char* smem_raw, const MonitorParams& P) {
+    constexpr int PS = Partials<KH>::kStride;
     const int rows = P.nbox * P.box_rows;
     const size_t tile_bytes = ((size_t)rows * 32 * sizeof(T) + 127) & ~(size_t)127;
-    const size_t work_bytes = kInPlace ? 0 : (((size_t)P.N * 32 * sizeof(float) + 127) & ~(size_t)127);
-    float* work = kInPlace ? reinterpret_cast<float*>(smem_raw) : reinterpret_cast<float*>(smem_raw + tile_bytes);
-    float* part = reinterpret_cast<float*>(smem_raw + tile_bytes + work_bytes);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(part + kNW * PS * 32);
+    const size_t work_bytes = sizeof(T) == 4 ? 0 : (((size_t)P.N * 32 * sizeof(float) + 127) & ~(size_t)127);
+    TileSmem L;
+    L.tile = smem_raw;
+    L.work = sizeof(T) == 4 ? reinterpret_cast<float*>(smem_raw) : reinterpret_cast<float*>(smem_raw + tile_bytes);
+    L.part = reinterpret_cast<float*>(smem_raw + tile_bytes + work_bytes);
+    (void)PS;
+    return L;
+}
+
+// One 32-pixel block (pixels 32*block .. 32*block+31 of the scene in P) by the
+// whole CTA (kNW warps).  tmap: tensor map of Y, or nullptr for plain loads.
+// bar/bar_uses: the CTA's tile-load mbarrier and how often it has completed.
+// Returns with every warp done with shared memory except for a final
+// barrier the caller places before the next block.
+template <int KH, typename T, bool kMask>
+__device__ __forceinline__ void simt_block(const CUtensorMap* tmap, const MonitorParams& P, int64_t block,
+                                           unsigned char* smem_raw, uint64_t* bar, uint32_t& bar_uses) {
+    using B = Basis<KH>;
+    constexpr int K = B::K, NB = B::NB, PS = Partials<KH>::kStride;
+    const TileSmem L = tile_smem<KH, T>(smem_raw, P);
+    T* tile = reinterpret_cast<T*>(L.tile);
+    float* work = L.work;
+    float* part = L.part;
+    const int rows = P.nbox * P.box_rows;
 
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
-    const int64_t p0 = (int64_t)blockIdx.x * 32;
+    const int64_t p0 = block * 32;
     const int64_t p = p0 + lane;
     const bool active = p < P.m;
     const int N = P.N;
 
     // ---- stage the [N][32] tile -------------------------------------------------------
-    if constexpr (kTMA) {
-        if (threadIdx.x == 0) {
-            ptx::prefetch_tmap(&tmap);
-            ptx::mbar_init(bar, 1);
-            ptx::fence_mbar_init();
-        }
-        __syncthreads();
+    if (tmap) {
         if (threadIdx.x == 0) {
             ptx::mbar_arrive_expect_tx(bar, (uint32_t)(rows * 32 * sizeof(T)));
             for (int b = 0; b < P.nbox; ++b)
-                ptx::tma_load_2d(tile + (size_t)b * P.box_rows * 32, &tmap, bar, (int)p0, b * P.box_rows);
+                ptx::tma_load_2d(tile + (size_t)b * P.box_rows * 32, tmap, bar, (int)p0, b * P.box_rows);
         }
-        if (!ptx::mbar_wait_bounded(bar, 0, kLoadWaitLimitNs)) {
+        const uint32_t parity = bar_uses & 1u;
+        ++bar_uses;
+        if (!__syncthreads_and(ptx::mbar_wait_bounded(bar, parity, kLoadWaitLimitNs))) {
             if (threadIdx.x == 0) atomicOr(&g_bfm_err, 1u);
             if (w == 0 && active) P.status[p] = BFM_PX_TIMEOUT;
-            ptx::mbar_wait_bounded(bar, 0, kLoadWaitLimitNs);  // let copies in flight land
+            ptx::mbar_wait_bounded(bar, parity, kLoadWaitLimitNs);  // let copies in flight land
             return;
         }
     } else {
@@ -149,7 +169,7 @@ __global__ void __launch_bounds__(kNW * 32) simt_kernel(const __grid_constant__ 
     }
 
     const float4* B4 = reinterpret_cast<const float4*>(P.basis);
-    const uint32_t* mrow = P.mask + blockIdx.x;
+    const uint32_t* mrow = P.mask + (p0 >> 5);
     auto obs = [&](int t, float& y) -> bool {
         bool v = Obs<T>::get(tile, t * 32 + lane, y);
         if constexpr (kMask) v = v && ((__ldg(mrow + (size_t)t * P.mask_words) >> lane) & 1u);
@@ -182,16 +202,92 @@ __global__ void __launch_bounds__(kNW * 32) simt_kernel(const __grid_constant__ 
     const int jhi = __reduce_max_sync(0xffffffffu, S.mycnt);
     phase7_mosum<KH>(sp, w, S, get_r, jlo, jhi, partf, getw);
     __syncthreads();
-    if (w != 0) return;
-    PixelOut<KH> o;
-    phase8_out<KH>(sp, S, partf, o);
-    if (!active) return;
-    P.status[p] = o.status;
-    P.brk[p] = o.brk;
-    P.mean[p] = o.mean;
-    P.sigma[p] = o.sigma;
+    if (w == 0) {
+        PixelOut<KH> o;
+        phase8_out<KH>(sp, S, partf, o);
+        if (active) {
+            P.status[p] = o.status;
+            P.brk[p] = o.brk;
+            P.mean[p] = o.mean;
+            P.sigma[p] = o.sigma;
 #pragma unroll
-    for (int i = 0; i < K; ++i) P.beta[(size_t)i * P.m + p] = o.beta[i];
+            for (int i = 0; i < K; ++i) P.beta[(size_t)i * P.m + p] = o.beta[i];
+        }
+    }
+}
+
+__device__ __forceinline__ uint64_t* tile_bar(unsigned char* smem_raw, size_t smem_bytes) {
+    return reinterpret_cast<uint64_t*>(smem_raw + smem_bytes - 16);
+}
+
+template <int KH, typename T, bool kTMA, bool kMask>
+__global__ void __launch_bounds__(kNW * 32) simt_kernel(const __grid_constant__ CUtensorMap tmap, const MonitorParams P,
+                                                       size_t smem_bytes) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* bar = tile_bar(smem_raw, smem_bytes);
+    if (kTMA && threadIdx.x == 0) {
+        ptx::prefetch_tmap(&tmap);
+        ptx::mbar_init(bar, 1);
+        ptx::fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t uses = 0;
+    simt_block<KH, T, kMask>(kTMA ? &tmap : nullptr, P, blockIdx.x, smem_raw, bar, uses);
+}
+
+// Persistent batched kernel: CTAs take 32-pixel blocks of any tile from a
+// device counter (`grab` at a time) until all `total` blocks are done.
+__global__ void __launch_bounds__(kNW * 32) batch_kernel(const BatchTileDesc* __restrict__ tiles,
+                                                        const CUtensorMap* __restrict__ tmaps, int ntiles,
+                                                        long long total, unsigned long long* counter, int grab,
+                                                        size_t smem_bytes) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ long long s_item;
+    uint64_t* bar = tile_bar(smem_raw, smem_bytes);
+    if (threadIdx.x == 0) {
+        ptx::mbar_init(bar, 1);
+        ptx::fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t uses = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, (unsigned long long)grab);
+        __syncthreads();
+        const long long it0 = s_item;
+        __syncthreads();
+        if (it0 >= total) break;
+        const long long it1 = it0 + grab < total ? it0 + grab : total;
+        for (long long it = it0; it < it1; ++it) {
+            int lo = 0, hi = ntiles - 1;  // last tile whose first block is <= it
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (tiles[mid].block0 <= it)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            const BatchTileDesc& T = tiles[lo];
+            const MonitorParams P = T.P;
+            const long long block = it - T.block0;
+            const CUtensorMap* tm = T.has_tma ? tmaps + lo : nullptr;
+            const int sel = (T.kh - 1) * 4 + (T.dtype == BFM_I16 ? 2 : 0) + (T.has_mask ? 1 : 0);
+            switch (sel) {
+                case 0: simt_block<1, float, false>(tm, P, block, smem_raw, bar, uses); break;
+                case 1: simt_block<1, float, true>(tm, P, block, smem_raw, bar, uses); break;
+                case 2: simt_block<1, int16_t, false>(tm, P, block, smem_raw, bar, uses); break;
+                case 3: simt_block<1, int16_t, true>(tm, P, block, smem_raw, bar, uses); break;
+                case 4: simt_block<2, float, false>(tm, P, block, smem_raw, bar, uses); break;
+                case 5: simt_block<2, float, true>(tm, P, block, smem_raw, bar, uses); break;
+                case 6: simt_block<2, int16_t, false>(tm, P, block, smem_raw, bar, uses); break;
+                case 7: simt_block<2, int16_t, true>(tm, P, block, smem_raw, bar, uses); break;
+                case 8: simt_block<3, float, false>(tm, P, block, smem_raw, bar, uses); break;
+                case 9: simt_block<3, float, true>(tm, P, block, smem_raw, bar, uses); break;
+                case 10: simt_block<3, int16_t, false>(tm, P, block, smem_raw, bar, uses); break;
+                default: simt_block<3, int16_t, true>(tm, P, block, smem_raw, bar, uses); break;
+            }
+            __syncthreads();
+        }
+    }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -221,7 +317,7 @@ bfm_status launch_one(const CUtensorMap& tm, const MonitorParams& P, size_t smem
         configured_dev[P.mask ? 1 : 0] = dev;
     }
     const unsigned grid = (unsigned)((P.m + 31) / 32);
-    kern<<<grid, kNW * 32, smem, stream>>>(tm, P);
+    kern<<<grid, kNW * 32, smem, stream>>>(tm, P, smem);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "simt kernel launch");
     return BFM_OK;
@@ -284,31 +380,63 @@ bfm_status launch_simt(const bfm_design_s* d, const void* Y, int dtype, const ui
     P.beta = beta;
     P.status = status;
 
-    const int elt = dtype == BFM_F32 ? 4 : 2;
     CUtensorMap tm;
     memset(&tm, 0, sizeof(tm));
-    bool tma = ((uintptr_t)Y % 16 == 0) && (((int64_t)m * elt) % 16 == 0) && m >= 32;
-    if (tma) {
-        auto enc = encode_fn();
-        if (!enc) {
-            tma = false;
-        } else {
-            cuuint64_t gdim[2] = {(cuuint64_t)m, (cuuint64_t)d->N};
-            cuuint64_t gstride[1] = {(cuuint64_t)m * elt};
-            cuuint32_t box[2] = {32u, (cuuint32_t)br};
-            cuuint32_t estride[2] = {1u, 1u};
-            CUresult r = enc(&tm, dtype == BFM_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16 /* same 16 bits */, 2,
-                             const_cast<void*>(Y), gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) tma = false;
-        }
-    }
+    const bool tma = make_tensor_map(&tm, Y, dtype, m, d->N, br);
     switch (d->k) {
         case 1: return dispatch_dtype<1>(dtype, tma, tm, P, smem, stream);
         case 2: return dispatch_dtype<2>(dtype, tma, tm, P, smem, stream);
         default: return dispatch_dtype<3>(dtype, tma, tm, P, smem, stream);
     }
+}
+
+bool make_tensor_map(CUtensorMap* tm, const void* Y, int dtype, int64_t m, int N, int box_rows) {
+    const int elt = dtype == BFM_F32 ? 4 : 2;
+    if ((uintptr_t)Y % 16 != 0 || ((int64_t)m * elt) % 16 != 0 || m < 32) return false;
+    auto enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t gdim[2] = {(cuuint64_t)m, (cuuint64_t)N};
+    cuuint64_t gstride[1] = {(cuuint64_t)m * elt};
+    cuuint32_t box[2] = {32u, (cuuint32_t)box_rows};
+    cuuint32_t estride[2] = {1u, 1u};
+    CUresult r = enc(tm, dtype == BFM_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 2,
+                     const_cast<void*>(Y), gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+bfm_status batch_launch_kernel(const void* tiles, const void* tmaps, int ntiles, int64_t total_blocks,
+                               unsigned long long* counter, int grab, int grid, size_t smem, cudaStream_t s,
+                               cudaGraph_t graph, const cudaGraphNode_t* dep, cudaGraphNode_t* node_out) {
+    static thread_local int configured = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (configured != dev) {
+        cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(batch_kernel)");
+        cudaFuncSetAttribute(batch_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        configured = dev;
+    }
+    const BatchTileDesc* t = static_cast<const BatchTileDesc*>(tiles);
+    const CUtensorMap* tm = static_cast<const CUtensorMap*>(tmaps);
+    long long total = (long long)total_blocks;
+    if (graph) {
+        void* args[] = {(void*)&t, (void*)&tm, (void*)&ntiles, (void*)&total, (void*)&counter, (void*)&grab,
+                        (void*)&smem};
+        cudaKernelNodeParams kp{};
+        kp.func = (void*)batch_kernel;
+        kp.gridDim = dim3((unsigned)grid);
+        kp.blockDim = dim3(kNW * 32);
+        kp.sharedMemBytes = (unsigned)smem;
+        kp.kernelParams = args;
+        cudaError_t e = cudaGraphAddKernelNode(node_out, graph, dep, dep ? 1 : 0, &kp);
+        if (e != cudaSuccess) return cuda_fail(e, "bfm_batch: kernel node");
+        return BFM_OK;
+    }
+    batch_kernel<<<grid, kNW * 32, smem, s>>>(t, tm, ntiles, total, counter, grab, smem);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "batch kernel launch");
+    return BFM_OK;
 }
 
 }  // namespace bfm

@@ -251,3 +251,12 @@ def workload_torch(name: str, *, m: int | None = None, device="cuda", dtype: str
                             device=device, **w["gen"])
     return dict(name=name, dates=d, Y=Y, true_break=brk, m=mm, N=w["N"], n_hist=w["n_hist"], f=w["f"],
                 k=w["k"], h_frac=w["h_frac"], lam=workload_lambda(name), dtype=dt)
+
+
+def lambda_for_horizon(T: float) -> float:
+    """lambda at alpha = 0.05, h = 0.25 for horizon T = N/n, linearly
+    interpolated in the stored grid (T in [1.2, 3.0], clamped)."""
+    grid = lambda_table()["grid_h0.25_alpha0.05"]
+    xs = sorted(float(k) for k in grid)
+    ys = [grid[f"{x:.1f}"] for x in xs]
+    return float(np.interp(min(max(T, xs[0]), xs[-1]), xs, ys))
