@@ -204,7 +204,7 @@ bfm_status bfm_batch_add(bfm_batch_t b, bfm_design_t d, const void* Y, int dtype
     }
     int br = 0, nb = 0;
     const size_t smem = simt_smem_bytes(d->N, d->k, dtype, &br, &nb);
-    if (smem == 0) {
+    if (smem == 0 || smem > 227 * 1024 - 256) {
         set_error("bfm_batch_add: the series does not fit one on-chip tile");
         return BFM_EUNSUPPORTED;
     }

@@ -412,7 +412,10 @@ bfm_status batch_launch_kernel(const void* tiles, const void* tmaps, int ntiles,
     int dev = 0;
     cudaGetDevice(&dev);
     if (configured != dev) {
-        cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaFuncAttributes fa{};
+        cudaFuncGetAttributes(&fa, batch_kernel);  // static shared memory counts against the 227 KB
+        cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             227 * 1024 - (int)fa.sharedSizeBytes);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(batch_kernel)");
         cudaFuncSetAttribute(batch_kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         configured = dev;
