@@ -209,6 +209,54 @@ bfm_status bfm_batch_set_config(bfm_batch_t b, int ctas_per_sm, int grab);
 int bfm_batch_tiles(bfm_batch_t b);
 bfm_status bfm_batch_destroy(bfm_batch_t b);
 
+/*
+ * bfm_batch_run_static -- a batch run that allocates nothing.  The paper has
+ * no counterpart; this is a deployment aid.
+ *
+ * Who needs it: callers that must not allocate device memory when they run
+ * work -- e.g. a serving process whose device memory is entirely reserved by
+ * its own pool allocator (a cudaMalloc outside the pool can fail or take
+ * memory the pool has already promised), or a latency-critical loop in which
+ * cudaMalloc/cudaFree would synchronise the device and stall other streams.
+ * bfm_batch_create/bfm_batch_run allocate a tile table, a work counter and a
+ * CUDA graph; this entry point instead keeps the tile table, the tensor maps
+ * and the work counter in one fixed array compiled into the library (about
+ * 17 KB of device memory, held by every GPU that loads the library until the
+ * process exits), and calls no cudaMalloc, cudaFree or allocating library
+ * routine.
+ *
+ *   tiles   host array of ntiles tile descriptions (same meaning and checks as
+ *           the arguments of bfm_batch_add; buffers are device pointers the
+ *           caller owns, designs stay alive until the work is done).
+ *   ntiles  0 <= ntiles <= BFM_STATIC_MAX_TILES; more is BFM_EINVAL with a
+ *           message (split the batch).
+ *   stream  work is enqueued on it: a copy of the tile table into the fixed
+ *           array, a reset of its work counter, the persistent kernel.
+ * Results equal those of bfm_monitor with BFM_ALGO_SIMT on each tile alone.
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture on the device.  Every call on a device
+ * shares the one array and overwrites it: two calls whose work overlaps on
+ * the GPU (different streams, no ordering between them) race and give wrong
+ * results -- order them on one stream or with events.
+ */
+#define BFM_STATIC_MAX_TILES 64
+typedef struct {
+    bfm_design_t design;
+    const void *Y;
+    int dtype;
+    const uint32_t *mask_bits;
+    int64_t m;
+    int n_hist;
+    double h_frac;
+    double lambda;
+    int32_t *break_idx;
+    float *mean_mosum;
+    float *sigma;
+    float *beta;
+    uint8_t *status;
+} bfm_tile_spec;
+bfm_status bfm_batch_run_static(const bfm_tile_spec *tiles, int ntiles, void *stream);
+
 /* Reads and clears the library's device error word (bit 0: a tile load wait
  * gave up).  Synchronises `stream`. */
 bfm_status bfm_device_errors(void *stream, uint32_t *bits);

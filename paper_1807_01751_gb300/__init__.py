@@ -32,6 +32,18 @@ _lock = threading.Lock()
 _lib = None
 
 
+BFM_STATIC_MAX_TILES = 64
+
+
+class TileSpec(ctypes.Structure):
+    """bfm_tile_spec of include/bfm.h (one tile of bfm_batch_run_static)."""
+    _fields_ = [("design", ctypes.c_void_p), ("Y", ctypes.c_void_p), ("dtype", ctypes.c_int),
+                ("mask_bits", ctypes.c_void_p), ("m", ctypes.c_int64), ("n_hist", ctypes.c_int),
+                ("h_frac", ctypes.c_double), ("lam", ctypes.c_double), ("break_idx", ctypes.c_void_p),
+                ("mean_mosum", ctypes.c_void_p), ("sigma", ctypes.c_void_p), ("beta", ctypes.c_void_p),
+                ("status", ctypes.c_void_p)]
+
+
 class BfmError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
@@ -91,6 +103,8 @@ def load(build_if_missing: bool = True):
         lib.bfm_batch_tiles.restype = i32
         lib.bfm_batch_destroy.argtypes = [vp]
         lib.bfm_batch_destroy.restype = i32
+        lib.bfm_batch_run_static.argtypes = [ctypes.POINTER(TileSpec), i32, vp]
+        lib.bfm_batch_run_static.restype = i32
         _lib = lib
         return lib
 
@@ -215,6 +229,22 @@ def bfm_batch_set_config(batch, ctas_per_sm: int, grab: int):
 
 def bfm_batch_destroy(batch):
     _check(load().bfm_batch_destroy(int(batch)))
+
+
+def bfm_batch_run_static(specs, stream=None):
+    """Run tiles (a list of TileSpec) through bfm_batch_run_static, the entry
+    point that allocates no device memory (for callers that cannot allocate
+    while they run work: pre-reserved memory pools, latency-critical loops)."""
+    arr = (TileSpec * max(1, len(specs)))(*specs)
+    _check(load().bfm_batch_run_static(arr, len(specs), _stream(stream)))
+
+
+def tile_spec(design, Y, *, n_hist: int, h_frac: float, lam: float, out: dict, mask_bits=None) -> TileSpec:
+    import torch
+    dtype = {torch.float32: BFM_F32, torch.int16: BFM_I16}[Y.dtype]
+    return TileSpec(int(design), _ptr(Y), dtype, _ptr(mask_bits), Y.shape[1], int(n_hist), float(h_frac), float(lam),
+                    _ptr(out["break_idx"]), _ptr(out["mean_mosum"]), _ptr(out["sigma"]), _ptr(out["beta"]),
+                    _ptr(out["status"]))
 
 
 # ---- convenience layer ----------------------------------------------------------
