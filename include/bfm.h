@@ -210,6 +210,60 @@ int bfm_batch_tiles(bfm_batch_t b);
 bfm_status bfm_batch_destroy(bfm_batch_t b);
 
 /*
+ * Serving loop (continuous admission under an HBM budget).  The paper runs
+ * one scene at a time (Algorithm 2); this is the serving extension.
+ *   bfm_serve_create   reserves `hbm_budget` bytes of device memory (one
+ *                      allocation; BFM_ENOMEM if it cannot) and `slots`
+ *                      streams (1..64), and starts the scheduler thread.
+ *   bfm_serve_submit   queues a tile; *ticket identifies it.  Requests are
+ *                      admitted in arrival order as soon as a slot is idle
+ *                      and the arena has room for its buffers (the input copy
+ *                      when y_on_host, and the five outputs); admitted
+ *                      requests run concurrently on the GPU.  BFM_EBUSY if
+ *                      the request alone exceeds the whole budget.
+ *   bfm_serve_poll     state: 0 pending, 1 running, 2 done, 3 failed,
+ *                      4 cancelled; latency from submission to completion
+ *                      (ms, -1 until done).  Returns the failure's status.
+ *   bfm_serve_result   device pointers of a done request's outputs (layout
+ *                      as bfm_monitor), valid until bfm_serve_release.
+ *   bfm_serve_release  frees a finished/failed/cancelled request's memory
+ *                      (results are device-resident until then).
+ *   bfm_serve_cancel   withdraws a request that is still pending.
+ *   bfm_serve_wait_all waits (bounded) until no request is pending/running.
+ *   bfm_serve_stats    p50/p99 latency of completed requests, their count
+ *                      and pixels, and the span from first arrival to last
+ *                      completion.
+ * Request fields: design (kept alive by the caller), Y (host when y_on_host,
+ * page-locked for the copy to overlap; else device), dtype, mask_bits
+ * (device or NULL), m, n_hist, h_frac, lambda as bfm_monitor; algo as
+ * bfm_monitor_ex (AUTO picks the tensor-core form when it applies).
+ */
+typedef struct bfm_server_s *bfm_server_t;
+typedef struct {
+    bfm_design_t design;
+    const void *Y;
+    int y_on_host;
+    int dtype;
+    const uint32_t *mask_bits;
+    int64_t m;
+    int n_hist;
+    double h_frac;
+    double lambda;
+    int algo;
+} bfm_serve_request;
+bfm_status bfm_serve_create(size_t hbm_budget, int slots, bfm_server_t *out);
+bfm_status bfm_serve_submit(bfm_server_t s, const bfm_serve_request *r, uint64_t *ticket);
+bfm_status bfm_serve_poll(bfm_server_t s, uint64_t ticket, int *state, double *latency_ms);
+bfm_status bfm_serve_result(bfm_server_t s, uint64_t ticket, int32_t **break_idx, float **mean_mosum,
+                            float **sigma, float **beta, uint8_t **status);
+bfm_status bfm_serve_release(bfm_server_t s, uint64_t ticket);
+bfm_status bfm_serve_cancel(bfm_server_t s, uint64_t ticket);
+bfm_status bfm_serve_wait_all(bfm_server_t s, double timeout_s);
+bfm_status bfm_serve_stats(bfm_server_t s, double *p50_ms, double *p99_ms, int64_t *completed, int64_t *pixels,
+                           double *span_ms);
+bfm_status bfm_serve_destroy(bfm_server_t s);
+
+/*
  * bfm_batch_run_static -- a batch run that allocates nothing.  The paper has
  * no counterpart; this is a deployment aid.
  *

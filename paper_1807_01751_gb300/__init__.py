@@ -44,6 +44,17 @@ class TileSpec(ctypes.Structure):
                 ("status", ctypes.c_void_p)]
 
 
+class ServeRequest(ctypes.Structure):
+    """bfm_serve_request of include/bfm.h."""
+    _fields_ = [("design", ctypes.c_void_p), ("Y", ctypes.c_void_p), ("y_on_host", ctypes.c_int),
+                ("dtype", ctypes.c_int), ("mask_bits", ctypes.c_void_p), ("m", ctypes.c_int64),
+                ("n_hist", ctypes.c_int), ("h_frac", ctypes.c_double), ("lam", ctypes.c_double),
+                ("algo", ctypes.c_int)]
+
+
+SERVE_STATES = {0: "pending", 1: "running", 2: "done", 3: "failed", 4: "cancelled"}
+
+
 class BfmError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
@@ -105,6 +116,19 @@ def load(build_if_missing: bool = True):
         lib.bfm_batch_destroy.restype = i32
         lib.bfm_batch_run_static.argtypes = [ctypes.POINTER(TileSpec), i32, vp]
         lib.bfm_batch_run_static.restype = i32
+        u64 = ctypes.c_uint64
+        P = ctypes.POINTER
+        lib.bfm_serve_create.argtypes = [sz, i32, P(vp)]
+        lib.bfm_serve_submit.argtypes = [vp, P(ServeRequest), P(u64)]
+        lib.bfm_serve_poll.argtypes = [vp, u64, P(i32), P(dbl)]
+        lib.bfm_serve_result.argtypes = [vp, u64, P(vp), P(vp), P(vp), P(vp), P(vp)]
+        lib.bfm_serve_release.argtypes = [vp, u64]
+        lib.bfm_serve_cancel.argtypes = [vp, u64]
+        lib.bfm_serve_wait_all.argtypes = [vp, dbl]
+        lib.bfm_serve_stats.argtypes = [vp, P(dbl), P(dbl), P(i64), P(i64), P(dbl)]
+        lib.bfm_serve_destroy.argtypes = [vp]
+        for n in ("create", "submit", "poll", "result", "release", "cancel", "wait_all", "stats", "destroy"):
+            getattr(lib, "bfm_serve_" + n).restype = i32
         _lib = lib
         return lib
 
@@ -328,6 +352,83 @@ class Batch:
     def close(self):
         if self.handle:
             bfm_batch_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _DeviceArray:
+    """Minimal __cuda_array_interface__ holder for a library-owned buffer."""
+
+    def __init__(self, ptr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+class Server:
+    """Owning wrapper of a bfm_server_t (continuous admission under an HBM
+    budget; results stay on the device until released)."""
+
+    def __init__(self, hbm_budget: int, slots: int = 4):
+        h = ctypes.c_void_p()
+        _check(load().bfm_serve_create(int(hbm_budget), int(slots), ctypes.byref(h)))
+        self.handle = h.value
+        self._keep = {}
+
+    def submit(self, design: Design, Y, *, n_hist: int, h_frac: float, lam: float, mask_bits=None,
+               algo: int = BFM_ALGO_AUTO) -> int:
+        import torch
+        dtype = {torch.float32: BFM_F32, torch.int16: BFM_I16}[Y.dtype]
+        req = ServeRequest(int(design), _ptr(Y), int(not Y.is_cuda), dtype, _ptr(mask_bits), int(Y.shape[1]),
+                           int(n_hist), float(h_frac), float(lam), int(algo))
+        t = ctypes.c_uint64(0)
+        _check(load().bfm_serve_submit(self.handle, ctypes.byref(req), ctypes.byref(t)))
+        self._keep[t.value] = (design, Y, mask_bits)
+        return t.value
+
+    def poll(self, ticket: int):
+        st, lat = ctypes.c_int(0), ctypes.c_double(0)
+        rc = load().bfm_serve_poll(self.handle, ticket, ctypes.byref(st), ctypes.byref(lat))
+        return SERVE_STATES[st.value], lat.value, rc
+
+    def result(self, ticket: int, K: int, m: int, copy: bool = True):
+        """The outputs of a done request: zero-copy views of the device-resident
+        buffers (valid until release), or copies when `copy`."""
+        import torch
+        ptrs = [ctypes.c_void_p() for _ in range(5)]
+        _check(load().bfm_serve_result(self.handle, ticket, *[ctypes.byref(p) for p in ptrs]))
+        spec = [("break_idx", "<i4", (m,)), ("mean_mosum", "<f4", (m,)), ("sigma", "<f4", (m,)),
+                ("beta", "<f4", (K, m)), ("status", "|u1", (m,))]
+        out = {}
+        for (name, ts, shape), p in zip(spec, ptrs):
+            v = torch.as_tensor(_DeviceArray(p.value or 0, shape, ts), device="cuda")
+            out[name] = v.clone() if copy else v
+        return out
+
+    def release(self, ticket: int):
+        _check(load().bfm_serve_release(self.handle, ticket))
+        self._keep.pop(ticket, None)
+
+    def cancel(self, ticket: int):
+        _check(load().bfm_serve_cancel(self.handle, ticket))
+
+    def wait_all(self, timeout_s: float = 60.0):
+        _check(load().bfm_serve_wait_all(self.handle, float(timeout_s)))
+
+    def stats(self):
+        p50, p99, span = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+        n, px = ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(load().bfm_serve_stats(self.handle, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(n),
+                                      ctypes.byref(px), ctypes.byref(span)))
+        return dict(p50_ms=p50.value, p99_ms=p99.value, completed=n.value, pixels=px.value, span_ms=span.value)
+
+    def close(self):
+        if self.handle:
+            _check(load().bfm_serve_destroy(self.handle))
             self.handle = 0
 
     def __del__(self):

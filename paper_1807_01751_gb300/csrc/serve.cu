@@ -1,0 +1,442 @@
+// Serving loop: continuous admission of scene tiles under an HBM budget.
+//
+// A server owns one device arena of `budget` bytes (a single cudaMalloc at
+// creation) and `slots` CUDA streams.  Requests enter a FIFO; a scheduler
+// thread admits the oldest request as soon as a slot is idle and the arena
+// has room for its buffers (input copy if the tile is on the host, and the
+// five outputs), enqueues on the slot's stream the host->device copy and the
+// per-pixel path, and a host callback that stamps completion.  Requests in
+// different slots run concurrently on the GPU; a request that arrives while
+// others run is admitted the moment a slot and memory free up.  Results stay
+// in the arena (device-resident) until the client releases them.  Designs are
+// shared through the library's design cache (one per date set).
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "bfm_internal.cuh"
+
+namespace bfm {
+
+bfm_status launch_simt(const bfm_design_s* d, const void* Y, int dtype, const uint32_t* mask, int64_t m, int n_hist,
+                       double h_frac, double lambda, int32_t* brk, float* mean, float* sigma, float* beta,
+                       uint8_t* status, cudaStream_t stream);
+
+namespace {
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+// First-fit allocator over [0, size) with 256-byte granules.
+class Arena {
+  public:
+    void reset(size_t size) {
+        size_ = size;
+        free_.clear();
+        free_[0] = size;
+    }
+    bool alloc(size_t bytes, size_t* off) {
+        bytes = (bytes + 255) & ~(size_t)255;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes, noff = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[noff] = rest;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = (bytes + 255) & ~(size_t)255;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t size() const { return size_; }
+    size_t largest() const {
+        size_t b = 0;
+        for (auto& kv : free_) b = std::max(b, kv.second);
+        return b;
+    }
+
+  private:
+    size_t size_ = 0;
+    std::map<size_t, size_t> free_;
+};
+
+enum { ST_PENDING = 0, ST_RUNNING = 1, ST_DONE = 2, ST_FAILED = 3, ST_CANCELLED = 4 };
+
+struct Req {
+    uint64_t ticket = 0;
+    bfm_serve_request r{};
+    int K = 0;
+    size_t bytes = 0, off = 0;
+    bool has_mem = false;
+    int state = ST_PENDING;
+    int slot = -1;
+    double t_arrive = 0, t_start = 0, t_done = 0;
+    bfm_status err = BFM_OK;
+    // device buffers inside the arena
+    void* y = nullptr;
+    int32_t* brk = nullptr;
+    float* mean = nullptr;
+    float* sigma = nullptr;
+    float* beta = nullptr;
+    uint8_t* status = nullptr;
+    struct bfm_server_s* srv = nullptr;
+};
+
+}  // namespace
+}  // namespace bfm
+
+struct bfm_server_s {
+    int device = -1;
+    unsigned char* arena = nullptr;
+    bfm::Arena alloc;
+    std::vector<cudaStream_t> streams;
+    std::vector<int> slot_busy;
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv, done_cv;
+    bool stop = false;
+    std::deque<bfm::Req*> pending;
+    std::map<uint64_t, bfm::Req*> reqs;
+    uint64_t next_ticket = 1;
+    std::vector<double> latencies;
+    int64_t completed = 0, pixels = 0;
+    double first_arrive = -1, last_done = 0;
+};
+
+namespace bfm {
+namespace {
+
+size_t req_bytes(const bfm_serve_request& r, int K) {
+    const size_t elt = r.dtype == BFM_F32 ? 4 : 2;
+    auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t b = a((size_t)r.m * (4 + 4 + 4 + 1)) + a((size_t)r.m * 4 * K) + 1024;
+    if (r.y_on_host) b += a((size_t)bfm_design_N(r.design) * r.m * elt);
+    return b;
+}
+
+void CUDART_CB on_done(void* p) {
+    Req* q = static_cast<Req*>(p);
+    bfm_server_s* s = q->srv;
+    std::lock_guard<std::mutex> lk(s->mu);
+    q->t_done = now_ms();
+    if (q->state == ST_RUNNING) q->state = ST_DONE;
+    s->slot_busy[q->slot] = 0;
+    s->latencies.push_back(q->t_done - q->t_arrive);
+    s->completed += 1;
+    s->pixels += q->r.m;
+    s->last_done = std::max(s->last_done, q->t_done);
+    s->cv.notify_all();
+    s->done_cv.notify_all();
+}
+
+// Called with the lock held.  Enqueues the request on slot `slot`.
+void start(bfm_server_s* s, Req* q, int slot) {
+    const bfm_serve_request& r = q->r;
+    unsigned char* base = s->arena + q->off;
+    auto a = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t o = 0;
+    q->brk = reinterpret_cast<int32_t*>(base + o);
+    o += a((size_t)r.m * 4);
+    q->mean = reinterpret_cast<float*>(base + o);
+    o += a((size_t)r.m * 4);
+    q->sigma = reinterpret_cast<float*>(base + o);
+    o += a((size_t)r.m * 4);
+    q->status = reinterpret_cast<uint8_t*>(base + o);
+    o += a((size_t)r.m);
+    q->beta = reinterpret_cast<float*>(base + o);
+    o += a((size_t)r.m * 4 * q->K);
+    const void* Y = r.Y;
+    cudaStream_t st = s->streams[slot];
+    q->slot = slot;
+    q->state = ST_RUNNING;
+    q->t_start = now_ms();
+    s->slot_busy[slot] = 1;
+    cudaError_t e = cudaSuccess;
+    if (r.y_on_host) {
+        const size_t elt = r.dtype == BFM_F32 ? 4 : 2;
+        q->y = base + o;
+        e = cudaMemcpyAsync(q->y, r.Y, (size_t)bfm_design_N(r.design) * r.m * elt, cudaMemcpyHostToDevice, st);
+        Y = q->y;
+    }
+    bfm_status bs = BFM_OK;
+    if (e != cudaSuccess) {
+        bs = cuda_fail(e, "serve: H2D");
+    } else if (r.m > 0) {
+        int algo = r.algo;
+        if (algo == BFM_ALGO_AUTO || algo == BFM_ALGO_MMA) {
+            const bool ok = mma_supported(r.design, r.dtype, r.n_hist, r.h_frac, nullptr);
+            algo = ok ? BFM_ALGO_MMA : BFM_ALGO_SIMT;
+        }
+        bs = algo == BFM_ALGO_MMA
+                 ? launch_mma(r.design, Y, r.mask_bits, r.m, r.n_hist, r.h_frac, r.lambda, q->brk, q->mean, q->sigma,
+                              q->beta, q->status, st)
+                 : launch_simt(r.design, Y, r.dtype, r.mask_bits, r.m, r.n_hist, r.h_frac, r.lambda, q->brk, q->mean,
+                               q->sigma, q->beta, q->status, st);
+    }
+    if (bs == BFM_OK) e = cudaLaunchHostFunc(st, on_done, q);
+    if (bs != BFM_OK || e != cudaSuccess) {
+        q->state = ST_FAILED;
+        q->err = bs != BFM_OK ? bs : BFM_ECUDA;
+        s->slot_busy[slot] = 0;
+    }
+}
+
+void worker_loop(bfm_server_s* s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (!s->stop) {
+        bool progress = false;
+        while (!s->pending.empty()) {
+            Req* q = s->pending.front();
+            if (q->state == ST_CANCELLED) {
+                s->pending.pop_front();
+                progress = true;
+                continue;
+            }
+            int slot = -1;
+            for (size_t i = 0; i < s->slot_busy.size(); ++i)
+                if (!s->slot_busy[i]) {
+                    slot = (int)i;
+                    break;
+                }
+            if (slot < 0) break;
+            size_t off = 0;
+            if (!s->alloc.alloc(q->bytes, &off)) break;  // FIFO: wait for memory
+            q->off = off;
+            q->has_mem = true;
+            s->pending.pop_front();
+            start(s, q, slot);
+            progress = true;
+        }
+        if (!progress) s->cv.wait(lk);
+    }
+}
+
+}  // namespace
+}  // namespace bfm
+
+using namespace bfm;
+
+extern "C" {
+
+bfm_status bfm_serve_create(size_t hbm_budget, int slots, bfm_server_t* out) {
+    if (!out || hbm_budget < 4096 || slots < 1 || slots > 64) {
+        set_error("bfm_serve_create: out NULL, budget below 4 KB or slots outside 1..64");
+        return BFM_EINVAL;
+    }
+    *out = nullptr;
+    auto* s = new bfm_server_s;
+    cudaGetDevice(&s->device);
+    cudaError_t e = cudaMalloc(&s->arena, hbm_budget);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete s;
+        set_error("bfm_serve_create: cannot reserve the HBM budget (" + std::to_string(hbm_budget) +
+                  " bytes): " + cudaGetErrorString(e));
+        return BFM_ENOMEM;
+    }
+    s->alloc.reset(hbm_budget);
+    s->streams.resize(slots);
+    s->slot_busy.assign(slots, 0);
+    for (auto& st : s->streams) cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    s->worker = std::thread(worker_loop, s);
+    *out = s;
+    return BFM_OK;
+}
+
+bfm_status bfm_serve_submit(bfm_server_t s, const bfm_serve_request* r, uint64_t* ticket) {
+    if (!s || !r || !r->design || !ticket) {
+        set_error("bfm_serve_submit: NULL server, request, design or ticket");
+        return BFM_EINVAL;
+    }
+    const bfm_design_s* d = r->design;
+    if ((r->dtype != BFM_F32 && r->dtype != BFM_I16) || r->m < 0 || !(r->n_hist >= 1 && r->n_hist < d->N) ||
+        !(r->h_frac > 0.0 && r->h_frac <= 1.0) || !(r->lambda > 0.0) || (r->m > 0 && !r->Y)) {
+        set_error("bfm_serve_submit: bad dtype, m, n_hist, h_frac, lambda or NULL Y");
+        return BFM_EINVAL;
+    }
+    auto* q = new Req;
+    q->r = *r;
+    q->K = d->K;
+    q->bytes = req_bytes(*r, d->K);
+    q->srv = s;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (q->bytes > s->alloc.size()) {
+        delete q;
+        set_error("bfm_serve_submit: the request needs more device memory than the whole budget");
+        return BFM_EBUSY;
+    }
+    q->ticket = s->next_ticket++;
+    q->t_arrive = now_ms();
+    if (s->first_arrive < 0) s->first_arrive = q->t_arrive;
+    s->reqs[q->ticket] = q;
+    s->pending.push_back(q);
+    *ticket = q->ticket;
+    s->cv.notify_all();
+    return BFM_OK;
+}
+
+bfm_status bfm_serve_poll(bfm_server_t s, uint64_t ticket, int* state, double* latency_ms) {
+    if (!s || !state) {
+        set_error("bfm_serve_poll: NULL server or state");
+        return BFM_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) {
+        set_error("bfm_serve_poll: unknown ticket");
+        return BFM_EINVAL;
+    }
+    *state = it->second->state;
+    if (latency_ms) *latency_ms = it->second->state == ST_DONE ? it->second->t_done - it->second->t_arrive : -1.0;
+    return it->second->state == ST_FAILED ? it->second->err : BFM_OK;
+}
+
+bfm_status bfm_serve_result(bfm_server_t s, uint64_t ticket, int32_t** break_idx, float** mean_mosum, float** sigma,
+                            float** beta, uint8_t** status) {
+    if (!s) {
+        set_error("bfm_serve_result: NULL server");
+        return BFM_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end() || it->second->state != ST_DONE) {
+        set_error("bfm_serve_result: unknown ticket or request not done");
+        return BFM_EINVAL;
+    }
+    Req* q = it->second;
+    if (break_idx) *break_idx = q->brk;
+    if (mean_mosum) *mean_mosum = q->mean;
+    if (sigma) *sigma = q->sigma;
+    if (beta) *beta = q->beta;
+    if (status) *status = q->status;
+    return BFM_OK;
+}
+
+bfm_status bfm_serve_release(bfm_server_t s, uint64_t ticket) {
+    if (!s) {
+        set_error("bfm_serve_release: NULL server");
+        return BFM_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) {
+        set_error("bfm_serve_release: unknown ticket");
+        return BFM_EINVAL;
+    }
+    Req* q = it->second;
+    if (q->state == ST_RUNNING || q->state == ST_PENDING) {
+        set_error("bfm_serve_release: request still pending or running (cancel or wait first)");
+        return BFM_EBUSY;
+    }
+    if (q->has_mem) s->alloc.release(q->off, q->bytes);
+    s->reqs.erase(it);
+    delete q;
+    s->cv.notify_all();
+    return BFM_OK;
+}
+
+bfm_status bfm_serve_cancel(bfm_server_t s, uint64_t ticket) {
+    if (!s) {
+        set_error("bfm_serve_cancel: NULL server");
+        return BFM_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->reqs.find(ticket);
+    if (it == s->reqs.end()) {
+        set_error("bfm_serve_cancel: unknown ticket");
+        return BFM_EINVAL;
+    }
+    if (it->second->state != ST_PENDING) {
+        set_error("bfm_serve_cancel: request already admitted");
+        return BFM_EBUSY;
+    }
+    it->second->state = ST_CANCELLED;
+    s->cv.notify_all();
+    return BFM_OK;
+}
+
+bfm_status bfm_serve_wait_all(bfm_server_t s, double timeout_s) {
+    if (!s) {
+        set_error("bfm_serve_wait_all: NULL server");
+        return BFM_EINVAL;
+    }
+    std::unique_lock<std::mutex> lk(s->mu);
+    auto busy = [&] {
+        for (auto& kv : s->reqs)
+            if (kv.second->state == ST_PENDING || kv.second->state == ST_RUNNING) return true;
+        return false;
+    };
+    const auto until = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
+    while (busy()) {
+        if (s->done_cv.wait_until(lk, until) == std::cv_status::timeout && busy()) {
+            set_error("bfm_serve_wait_all: timed out");
+            return BFM_ETIMEOUT;
+        }
+    }
+    return BFM_OK;
+}
+
+bfm_status bfm_serve_stats(bfm_server_t s, double* p50_ms, double* p99_ms, int64_t* completed, int64_t* pixels,
+                           double* span_ms) {
+    if (!s) {
+        set_error("bfm_serve_stats: NULL server");
+        return BFM_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    std::vector<double> v = s->latencies;
+    std::sort(v.begin(), v.end());
+    auto q = [&](double f) { return v.empty() ? 0.0 : v[std::min(v.size() - 1, (size_t)(f * (double)v.size()))]; };
+    if (p50_ms) *p50_ms = q(0.5);
+    if (p99_ms) *p99_ms = q(0.99);
+    if (completed) *completed = s->completed;
+    if (pixels) *pixels = s->pixels;
+    if (span_ms) *span_ms = s->first_arrive < 0 ? 0.0 : s->last_done - s->first_arrive;
+    return BFM_OK;
+}
+
+bfm_status bfm_serve_destroy(bfm_server_t s) {
+    if (!s) {
+        set_error("bfm_serve_destroy: NULL server");
+        return BFM_EINVAL;
+    }
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        s->cv.notify_all();
+    }
+    s->worker.join();
+    for (auto st : s->streams) {
+        cudaStreamSynchronize(st);
+        cudaStreamDestroy(st);
+    }
+    for (auto& kv : s->reqs) delete kv.second;
+    cudaFree(s->arena);
+    delete s;
+    return BFM_OK;
+}
+
+}  // extern "C"
