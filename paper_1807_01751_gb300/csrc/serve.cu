@@ -11,7 +11,9 @@
 // in the arena (device-resident) until the client releases them.  Designs are
 // shared through the library's design cache (one per date set).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <memory>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -32,6 +34,11 @@ namespace {
 double now_ms() {
     using namespace std::chrono;
     return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+int64_t now_ns() {
+    using namespace std::chrono;
+    return duration_cast<nanoseconds>(steady_clock::now().time_since_epoch()).count();
 }
 
 // First-fit allocator over [0, size) with 256-byte granules.
@@ -91,9 +98,11 @@ struct Req {
     int K = 0;
     size_t bytes = 0, off = 0;
     bool has_mem = false;
-    int state = ST_PENDING;
+    bool accounted = false;             // completion counted in the statistics
+    std::atomic<int> state{ST_PENDING};  // DONE is stored by the completion callback
     int slot = -1;
-    double t_arrive = 0, t_start = 0, t_done = 0;
+    double t_arrive = 0, t_start = 0;
+    std::atomic<int64_t> t_done_ns{0};
     bfm_status err = BFM_OK;
     // device buffers inside the arena
     void* y = nullptr;
@@ -113,12 +122,14 @@ struct bfm_server_s {
     unsigned char* arena = nullptr;
     bfm::Arena alloc;
     std::vector<cudaStream_t> streams;
-    std::vector<int> slot_busy;
+    std::unique_ptr<std::atomic<int>[]> slot_busy;  // cleared by the completion callback
+    int nslots = 0;
     std::thread worker;
     std::mutex mu;
     std::condition_variable cv, done_cv;
     bool stop = false;
     std::deque<bfm::Req*> pending;
+    std::vector<bfm::Req*> running;
     std::map<uint64_t, bfm::Req*> reqs;
     uint64_t next_ticket = 1;
     std::vector<double> latencies;
@@ -137,22 +148,46 @@ size_t req_bytes(const bfm_serve_request& r, int K) {
     return b;
 }
 
+// Host callback at the end of a request's stream work.  It runs on a driver
+// thread and must neither call CUDA nor block: it only publishes atomics and
+// wakes the scheduler; the bookkeeping happens in the scheduler thread.
 void CUDART_CB on_done(void* p) {
     Req* q = static_cast<Req*>(p);
     bfm_server_s* s = q->srv;
-    std::lock_guard<std::mutex> lk(s->mu);
-    q->t_done = now_ms();
-    if (q->state == ST_RUNNING) q->state = ST_DONE;
-    s->slot_busy[q->slot] = 0;
-    s->latencies.push_back(q->t_done - q->t_arrive);
-    s->completed += 1;
-    s->pixels += q->r.m;
-    s->last_done = std::max(s->last_done, q->t_done);
+    const int slot = q->slot;
+    q->t_done_ns.store(now_ns());
+    s->slot_busy[slot].store(0);
+    q->state.store(ST_DONE);  // last access to q: a client may release it from now on
     s->cv.notify_all();
     s->done_cv.notify_all();
 }
 
-// Called with the lock held.  Enqueues the request on slot `slot`.
+double done_ms(const Req* q) { return (double)q->t_done_ns.load() * 1e-6; }
+
+// With the lock held: move finished requests out of `running` into the statistics.
+void account(bfm_server_s* s) {
+    for (size_t i = 0; i < s->running.size();) {
+        Req* q = s->running[i];
+        const int st = q->state.load();
+        if (st == ST_DONE || st == ST_FAILED) {
+            if (st == ST_DONE && !q->accounted) {
+                const double td = done_ms(q);
+                s->latencies.push_back(td - q->t_arrive);
+                s->completed += 1;
+                s->pixels += q->r.m;
+                s->last_done = std::max(s->last_done, td);
+            }
+            q->accounted = true;
+            s->running[i] = s->running.back();
+            s->running.pop_back();
+        } else {
+            ++i;
+        }
+    }
+}
+
+// Called WITHOUT the lock (CUDA calls only): enqueues the admitted request on
+// its slot's stream.  The request cannot be released while RUNNING.
 void start(bfm_server_s* s, Req* q, int slot) {
     const bfm_serve_request& r = q->r;
     unsigned char* base = s->arena + q->off;
@@ -170,10 +205,6 @@ void start(bfm_server_s* s, Req* q, int slot) {
     o += a((size_t)r.m * 4 * q->K);
     const void* Y = r.Y;
     cudaStream_t st = s->streams[slot];
-    q->slot = slot;
-    q->state = ST_RUNNING;
-    q->t_start = now_ms();
-    s->slot_busy[slot] = 1;
     cudaError_t e = cudaSuccess;
     if (r.y_on_host) {
         const size_t elt = r.dtype == BFM_F32 ? 4 : 2;
@@ -198,9 +229,9 @@ void start(bfm_server_s* s, Req* q, int slot) {
     }
     if (bs == BFM_OK) e = cudaLaunchHostFunc(st, on_done, q);
     if (bs != BFM_OK || e != cudaSuccess) {
-        q->state = ST_FAILED;
         q->err = bs != BFM_OK ? bs : BFM_ECUDA;
-        s->slot_busy[slot] = 0;
+        q->state.store(ST_FAILED);
+        s->slot_busy[slot].store(0);
     }
 }
 
@@ -208,18 +239,19 @@ void worker_loop(bfm_server_s* s) {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
     while (!s->stop) {
-        bool progress = false;
+        account(s);
+        // admit in arrival order while a slot is idle and memory allows
+        std::vector<std::pair<Req*, int>> to_start;
         while (!s->pending.empty()) {
             Req* q = s->pending.front();
-            if (q->state == ST_CANCELLED) {
+            if (q->state.load() == ST_CANCELLED) {
                 s->pending.pop_front();
-                progress = true;
                 continue;
             }
             int slot = -1;
-            for (size_t i = 0; i < s->slot_busy.size(); ++i)
-                if (!s->slot_busy[i]) {
-                    slot = (int)i;
+            for (int i = 0; i < s->nslots; ++i)
+                if (s->slot_busy[i].load() == 0) {
+                    slot = i;
                     break;
                 }
             if (slot < 0) break;
@@ -227,11 +259,21 @@ void worker_loop(bfm_server_s* s) {
             if (!s->alloc.alloc(q->bytes, &off)) break;  // FIFO: wait for memory
             q->off = off;
             q->has_mem = true;
+            q->slot = slot;
+            q->t_start = now_ms();
+            q->state.store(ST_RUNNING);
+            s->slot_busy[slot].store(1);
             s->pending.pop_front();
-            start(s, q, slot);
-            progress = true;
+            s->running.push_back(q);
+            to_start.emplace_back(q, slot);
         }
-        if (!progress) s->cv.wait(lk);
+        if (!to_start.empty()) {
+            lk.unlock();  // no CUDA call is made while the lock is held
+            for (auto& qs : to_start) start(s, qs.first, qs.second);
+            lk.lock();
+            continue;
+        }
+        s->cv.wait_for(lk, std::chrono::milliseconds(2));
     }
 }
 
@@ -260,7 +302,9 @@ bfm_status bfm_serve_create(size_t hbm_budget, int slots, bfm_server_t* out) {
     }
     s->alloc.reset(hbm_budget);
     s->streams.resize(slots);
-    s->slot_busy.assign(slots, 0);
+    s->nslots = slots;
+    s->slot_busy.reset(new std::atomic<int>[slots]);
+    for (int i = 0; i < slots; ++i) s->slot_busy[i].store(0);
     for (auto& st : s->streams) cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     s->worker = std::thread(worker_loop, s);
     *out = s;
@@ -310,9 +354,10 @@ bfm_status bfm_serve_poll(bfm_server_t s, uint64_t ticket, int* state, double* l
         set_error("bfm_serve_poll: unknown ticket");
         return BFM_EINVAL;
     }
-    *state = it->second->state;
-    if (latency_ms) *latency_ms = it->second->state == ST_DONE ? it->second->t_done - it->second->t_arrive : -1.0;
-    return it->second->state == ST_FAILED ? it->second->err : BFM_OK;
+    const int st = it->second->state.load();
+    *state = st;
+    if (latency_ms) *latency_ms = st == ST_DONE ? done_ms(it->second) - it->second->t_arrive : -1.0;
+    return st == ST_FAILED ? it->second->err : BFM_OK;
 }
 
 bfm_status bfm_serve_result(bfm_server_t s, uint64_t ticket, int32_t** break_idx, float** mean_mosum, float** sigma,
@@ -323,7 +368,7 @@ bfm_status bfm_serve_result(bfm_server_t s, uint64_t ticket, int32_t** break_idx
     }
     std::lock_guard<std::mutex> lk(s->mu);
     auto it = s->reqs.find(ticket);
-    if (it == s->reqs.end() || it->second->state != ST_DONE) {
+    if (it == s->reqs.end() || it->second->state.load() != ST_DONE) {
         set_error("bfm_serve_result: unknown ticket or request not done");
         return BFM_EINVAL;
     }
@@ -348,10 +393,12 @@ bfm_status bfm_serve_release(bfm_server_t s, uint64_t ticket) {
         return BFM_EINVAL;
     }
     Req* q = it->second;
-    if (q->state == ST_RUNNING || q->state == ST_PENDING) {
+    const int st = q->state.load();
+    if (st == ST_RUNNING || st == ST_PENDING) {
         set_error("bfm_serve_release: request still pending or running (cancel or wait first)");
         return BFM_EBUSY;
     }
+    account(s);  // make sure the worker's bookkeeping no longer refers to it
     if (q->has_mem) s->alloc.release(q->off, q->bytes);
     s->reqs.erase(it);
     delete q;
@@ -370,11 +417,11 @@ bfm_status bfm_serve_cancel(bfm_server_t s, uint64_t ticket) {
         set_error("bfm_serve_cancel: unknown ticket");
         return BFM_EINVAL;
     }
-    if (it->second->state != ST_PENDING) {
+    int expect = ST_PENDING;
+    if (!it->second->state.compare_exchange_strong(expect, ST_CANCELLED)) {
         set_error("bfm_serve_cancel: request already admitted");
         return BFM_EBUSY;
     }
-    it->second->state = ST_CANCELLED;
     s->cv.notify_all();
     return BFM_OK;
 }
@@ -386,17 +433,21 @@ bfm_status bfm_serve_wait_all(bfm_server_t s, double timeout_s) {
     }
     std::unique_lock<std::mutex> lk(s->mu);
     auto busy = [&] {
-        for (auto& kv : s->reqs)
-            if (kv.second->state == ST_PENDING || kv.second->state == ST_RUNNING) return true;
+        for (auto& kv : s->reqs) {
+            const int st = kv.second->state.load();
+            if (st == ST_PENDING || st == ST_RUNNING) return true;
+        }
         return false;
     };
     const auto until = std::chrono::steady_clock::now() + std::chrono::duration<double>(timeout_s);
     while (busy()) {
-        if (s->done_cv.wait_until(lk, until) == std::cv_status::timeout && busy()) {
+        if (std::chrono::steady_clock::now() >= until) {
             set_error("bfm_serve_wait_all: timed out");
             return BFM_ETIMEOUT;
         }
+        s->done_cv.wait_for(lk, std::chrono::milliseconds(2));
     }
+    account(s);
     return BFM_OK;
 }
 
@@ -407,6 +458,7 @@ bfm_status bfm_serve_stats(bfm_server_t s, double* p50_ms, double* p99_ms, int64
         return BFM_EINVAL;
     }
     std::lock_guard<std::mutex> lk(s->mu);
+    account(s);
     std::vector<double> v = s->latencies;
     std::sort(v.begin(), v.end());
     auto q = [&](double f) { return v.empty() ? 0.0 : v[std::min(v.size() - 1, (size_t)(f * (double)v.size()))]; };
