@@ -93,7 +93,8 @@ def test_refusals_and_cancellation(bfm):
     tiles = _tiles(count=4, scale=0.01)
     d = bfm.Design(tiles[0]["dates"], tiles[0]["k"], 23.0)
     Y = torch.from_numpy(tiles[0]["Y"]).cuda()
-    small = bfm.Server(hbm_budget=64 * 1024, slots=1)
+    small = bfm.Server(hbm_budget=4096, slots=1)  # smaller than any request's outputs
+    assert tiles[0]["m"] >= 100
     with pytest.raises(bfm.BfmError) as ei:
         small.submit(d, Y, n_hist=tiles[0]["n_hist"], h_frac=0.25, lam=1.7)
     assert ei.value.code == 5  # BFM_EBUSY: larger than the whole budget
