@@ -19,10 +19,10 @@
 //            TMEM[c] += r0 x Phi: one refinement step beta = beta0 + G^-1 c;
 //            sum r^2 = sum r0^2 - delta'c (sigma-hat, Algorithm 1 step 5)
 //   yhat     TMEM[Y] += [delta_hi | delta_lo] x Phi (yhat = yhat0 + X delta)
-//   MOSUM    per thread, date by date: r = y - yhat, valid residuals in a
-//            ring of h+1, the window sum of h valid residuals (Eq. 3) kept
-//            compensated, first crossing of lambda*sqrt(log+(j/n)) (Eq. 4)
-//            and the mean
+//   MOSUM    per thread, 32 dates at a time: r = y - yhat, compensated
+//            prefix sums S over valid positions in a ring, windows of h
+//            valid residuals W = S_J - S_{J-h} (Eq. 3), first crossing of
+//            lambda*sqrt(log+(j/n)) (Eq. 4) and the mean
 //
 // Scaling: A operands carry beta/16 and r0/4 (exact powers of two) so that
 // fp16 holds any int16-scale value; results are scaled back exactly.
@@ -126,7 +126,7 @@ __device__ __forceinline__ void mma_yhat(uint32_t dcol, const unsigned char* bhi
 }
 
 template <int KH, bool kTMA, bool kMask>
-__global__ void __launch_bounds__(kTile) mma_kernel(const __grid_constant__ CUtensorMap tmap, const MmaParams P) {
+__global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ CUtensorMap tmap, const MmaParams P) {
     using B = Basis<KH>;
     constexpr int K = B::K, NBR = B::NBR;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -385,42 +385,73 @@ __global__ void __launch_bounds__(kTile) mma_kernel(const __grid_constant__ CUte
     }
     ok &= wait_done();
 
-    // ---- MOSUM, date by date --------------------------------------------------------------------
+    // ---- MOSUM, 32 dates at a time ------------------------------------------------------
+    // Per chunk: residuals and validity independently; then the compensated
+    // prefix sums S_J over valid positions go to a ring of R >= h + 33 slots
+    // (this chunk's writes all land before its reads); then every window
+    // W_J = S_J - S_{J-h} of the chunk's monitoring positions (Eq. 3) is an
+    // independent difference, tested against lambda*sqrt(log+(J/n)) (Eq. 4).
     float* ring = reinterpret_cast<float*>(sA);  // [P.ring][128], free now
     const int R = P.ring;
-    const int wstart = n_i - h;
     int j = 0, slot = 0, brk = -1;
-    float W = 0.f, Wc = 0.f, sumW = 0.f, sumWc = 0.f;
+    float Sh = 0.f, Sc = 0.f;                       // running prefix sum (compensated)
+    float m0 = 0.f, m0c = 0.f, m1 = 0.f, m1c = 0.f;  // two interleaved sums of W
     for (int c0 = 0; c0 < N; c0 += 32) {
         float yh[32];
         ptx::tmem_ld32(tmem + lane_base + kColY + (uint32_t)c0, yh);
+        float r[32];
+        uint32_t vbits = 0u;
 #pragma unroll
         for (int e = 0; e < 32; ++e) {
             const int t = c0 + e;
             int y = 0;
             const bool v = t < N && obs(t, y);
-            if (v) {
-                const float r = (float)y - 16.f * yh[e];
-                if (t < n_hist) {
-                    if (j >= wstart) comp_add(W, Wc, r);
-                } else {
-                    int ls = slot - h;
-                    if (ls < 0) ls += R;
-                    const float lag = ring[ls * kTile + tid];
-                    comp_add(W, Wc, r - lag);
-                    const float wv = W + Wc;
-                    const int J = j + 1;
-                    float th = thr;
-                    if (J > jlim) th = thr * sqrtf(logf((float)J / (float)n_i));
-                    if (brk < 0 && fabsf(wv) > th) brk = t;
-                    comp_add(sumW, sumWc, wv);
-                }
-                ring[slot * kTile + tid] = r;
+            r[e] = (float)y - 16.f * yh[e];
+            vbits |= (v ? 1u : 0u) << e;
+        }
+        float Sv[32];
+        int sl[32], jj[32];
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+            if ((vbits >> e) & 1u) {
+                comp_add(Sh, Sc, r[e]);
+                Sv[e] = Sh + Sc;
+                ring[slot * kTile + tid] = Sv[e];
+                sl[e] = slot;
+                jj[e] = j;
                 ++j;
                 if (++slot == R) slot = 0;
+            } else {
+                Sv[e] = 0.f;
+                sl[e] = 0;
+                jj[e] = 0;
             }
         }
+        // monitoring positions of this chunk: dates >= n_hist
+        const uint32_t mon = c0 + 32 <= n_hist ? 0u : (c0 >= n_hist ? 0xffffffffu : (0xffffffffu << (n_hist - c0)));
+        const uint32_t mv = vbits & mon;
+        uint32_t cross = 0u;
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+            if ((mv >> e) & 1u) {
+                int ls = sl[e] - h;
+                if (ls < 0) ls += R;
+                const float W = Sv[e] - ring[ls * kTile + tid];
+                const int J = jj[e] + 1;
+                float th = thr;
+                if (J > jlim) th = thr * sqrtf(logf((float)J / (float)n_i));
+                cross |= (fabsf(W) > th ? 1u : 0u) << e;
+                if (e & 1)
+                    comp_add(m1, m1c, W);
+                else
+                    comp_add(m0, m0c, W);
+            }
+        }
+        if (brk < 0 && cross) brk = c0 + __ffs(cross) - 1;
     }
+    float sumW = m0, sumWc = m0c;
+    comp_add(sumW, sumWc, m1);
+    sumWc += m1c;
     const int N_i = j;
 
     // ---- outputs ------------------------------------------------------------------------------
@@ -492,11 +523,13 @@ size_t mma_smem(int N, int npad, int* box_rows, int* nbox) {
     return y + tc_phi_bytes(npad) + 2 * (size_t)kBufBytes + 64;
 }
 
+// Ring of prefix sums: the h slots behind the oldest new position of a
+// 32-date chunk must survive the chunk's writes.
 int ring_len(int n_hist, double h_frac) {
     int hmax = (int)std::floor(h_frac * (double)n_hist);
     if (hmax < 1) hmax = 1;
     if (hmax > n_hist) hmax = n_hist;
-    return hmax + 1;
+    return hmax + 33;
 }
 
 template <int KH, bool kTMA>
