@@ -328,7 +328,7 @@ bfm_status bfm_monitor_ex(bfm_design_t d, const void* Y, int dtype, const uint32
     }
     const bool mma_ok = mma_supported(d, dtype, n_hist, h_frac, nullptr);
     if (algo == BFM_ALGO_MMA && !mma_ok) {
-        set_error("bfm_monitor: the tensor-core form needs int16 storage, N <= 448 and a bandwidth of at most 63 "
+        set_error("bfm_monitor: the tensor-core form needs int16 storage, N <= 448 and a bandwidth of at most 87 "
                   "observations");
         return BFM_EUNSUPPORTED;
     }

@@ -19,7 +19,7 @@
 //            TMEM[c] += r0 x Phi: one refinement step beta = beta0 + G^-1 c;
 //            sum r^2 = sum r0^2 - delta'c (sigma-hat, Algorithm 1 step 5)
 //   yhat     TMEM[Y] += [delta_hi | delta_lo] x Phi (yhat = yhat0 + X delta)
-//   MOSUM    per thread, 32 dates at a time: r = y - yhat, compensated
+//   MOSUM    per thread, 8 dates at a time: r = y - yhat, compensated
 //            prefix sums S over valid positions in a ring, windows of h
 //            valid residuals W = S_J - S_{J-h} (Eq. 3), first crossing of
 //            lambda*sqrt(log+(j/n)) (Eq. 4) and the mean
@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
         const int buf = c & 1;
         unsigned char* pl = sA + (size_t)buf * kBufBytes;
         if (c >= 2) ok &= ptx::mbar_wait_bounded(bar_a + buf, (uint32_t)(((c >> 1) - 1) & 1), kWaitNs);
-#pragma unroll
+#pragma unroll 1
         for (int g = 0; g < kChunk / 8; ++g) {
             float mk[8], a1[8], a2[8];
 #pragma unroll
@@ -311,18 +311,17 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
         const int buf = c & 1;
         unsigned char* pl = sA + (size_t)buf * kBufBytes;
         if (c >= 2) ok &= ptx::mbar_wait_bounded(bar_r + buf, (uint32_t)(((c >> 1) - 1) & 1), kWaitNs);
-        float yh[32];
-        ptx::tmem_ld32(tmem + lane_base + kColY + (uint32_t)(c * kChunk), yh);
-#pragma unroll
+#pragma unroll 1
         for (int g = 0; g < kChunk / 8; ++g) {
-            float rh[8], rl[8];
+            float yh[8], rh[8], rl[8];
+            ptx::tmem_ld8(tmem + lane_base + kColY + (uint32_t)(c * kChunk + g * 8), yh);
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const int t = c * kChunk + g * 8 + e;
                 int y = 0;
                 bool v = false;
                 if (t < n_hist) v = obs(t, y);
-                const float r0 = v ? ((float)y - 16.f * yh[g * 8 + e]) : 0.f;
+                const float r0 = v ? ((float)y - 16.f * yh[e]) : 0.f;
                 ss = fmaf(r0, r0, ss);
                 const float r4 = r0 * 0.25f;
                 rh[e] = __half2float(__float2half_rn(r4));
@@ -385,67 +384,64 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
     }
     ok &= wait_done();
 
-    // ---- MOSUM, 32 dates at a time ------------------------------------------------------
-    // Per chunk: residuals and validity independently; then the compensated
-    // prefix sums S_J over valid positions go to a ring of R >= h + 33 slots
-    // (this chunk's writes all land before its reads); then every window
-    // W_J = S_J - S_{J-h} of the chunk's monitoring positions (Eq. 3) is an
-    // independent difference, tested against lambda*sqrt(log+(J/n)) (Eq. 4).
+    // ---- MOSUM, 8 dates at a time ---------------------------------------------------------
+    // Per group: residuals and validity independently; the compensated prefix
+    // sums S_J over valid positions go to a ring of R >= h + 9 slots (the
+    // group's writes all land before its reads); then each window
+    // W_J = S_J - S_{J-h} of the group's monitoring positions (Eq. 3) is an
+    // independent difference tested against lambda*sqrt(log+(J/n)) (Eq. 4).
+    // Branch-free: invalid dates add 0 and their (in-range) lag reads are masked.
     float* ring = reinterpret_cast<float*>(sA);  // [P.ring][128], free now
     const int R = P.ring;
     int j = 0, slot = 0, brk = -1;
     float Sh = 0.f, Sc = 0.f;                       // running prefix sum (compensated)
     float m0 = 0.f, m0c = 0.f, m1 = 0.f, m1c = 0.f;  // two interleaved sums of W
-    for (int c0 = 0; c0 < N; c0 += 32) {
-        float yh[32];
-        ptx::tmem_ld32(tmem + lane_base + kColY + (uint32_t)c0, yh);
-        float r[32];
-        uint32_t vbits = 0u;
+#pragma unroll 1
+    for (int c0 = 0; c0 < N; c0 += 8) {
+        float yh[8];
+        ptx::tmem_ld8(tmem + lane_base + kColY + (uint32_t)c0, yh);
+        float r[8];
+        uint32_t vb = 0u;
 #pragma unroll
-        for (int e = 0; e < 32; ++e) {
+        for (int e = 0; e < 8; ++e) {
             const int t = c0 + e;
             int y = 0;
             const bool v = t < N && obs(t, y);
             r[e] = (float)y - 16.f * yh[e];
-            vbits |= (v ? 1u : 0u) << e;
+            vb |= (v ? 1u : 0u) << e;
         }
-        float Sv[32];
-        int sl[32], jj[32];
+        float Sv[8];
+        int sl[8], jj[8];
 #pragma unroll
-        for (int e = 0; e < 32; ++e) {
-            if ((vbits >> e) & 1u) {
-                comp_add(Sh, Sc, r[e]);
-                Sv[e] = Sh + Sc;
-                ring[slot * kTile + tid] = Sv[e];
-                sl[e] = slot;
-                jj[e] = j;
-                ++j;
-                if (++slot == R) slot = 0;
-            } else {
-                Sv[e] = 0.f;
-                sl[e] = 0;
-                jj[e] = 0;
-            }
+        for (int e = 0; e < 8; ++e) {
+            const int v = (vb >> e) & 1u;
+            comp_add(Sh, Sc, v ? r[e] : 0.f);
+            Sv[e] = Sh + Sc;
+            if (v) ring[slot * kTile + tid] = Sv[e];
+            sl[e] = slot;
+            jj[e] = j;
+            j += v;
+            slot += v;
+            slot = slot == R ? 0 : slot;
         }
-        // monitoring positions of this chunk: dates >= n_hist
-        const uint32_t mon = c0 + 32 <= n_hist ? 0u : (c0 >= n_hist ? 0xffffffffu : (0xffffffffu << (n_hist - c0)));
-        const uint32_t mv = vbits & mon;
+        const int d = n_hist - c0;  // monitoring dates of the group: e >= d
+        const uint32_t mon = d <= 0 ? 0xffu : (d >= 8 ? 0u : (0xffu << d) & 0xffu);
+        const uint32_t mv = vb & mon;
         uint32_t cross = 0u;
 #pragma unroll
-        for (int e = 0; e < 32; ++e) {
-            if ((mv >> e) & 1u) {
-                int ls = sl[e] - h;
-                if (ls < 0) ls += R;
-                const float W = Sv[e] - ring[ls * kTile + tid];
-                const int J = jj[e] + 1;
-                float th = thr;
-                if (J > jlim) th = thr * sqrtf(logf((float)J / (float)n_i));
-                cross |= (fabsf(W) > th ? 1u : 0u) << e;
-                if (e & 1)
-                    comp_add(m1, m1c, W);
-                else
-                    comp_add(m0, m0c, W);
-            }
+        for (int e = 0; e < 8; ++e) {
+            int ls = sl[e] - h;
+            ls += ls < 0 ? R : 0;
+            const float W = Sv[e] - ring[ls * kTile + tid];
+            const int J = jj[e] + 1;
+            float th = thr;
+            if (J > jlim) th = thr * sqrtf(logf((float)J / (float)n_i));
+            const bool m = (mv >> e) & 1u;
+            cross |= ((m && fabsf(W) > th) ? 1u : 0u) << e;
+            if (e & 1)
+                comp_add(m1, m1c, m ? W : 0.f);
+            else
+                comp_add(m0, m0c, m ? W : 0.f);
         }
         if (brk < 0 && cross) brk = c0 + __ffs(cross) - 1;
     }
@@ -523,13 +519,13 @@ size_t mma_smem(int N, int npad, int* box_rows, int* nbox) {
     return y + tc_phi_bytes(npad) + 2 * (size_t)kBufBytes + 64;
 }
 
-// Ring of prefix sums: the h slots behind the oldest new position of a
-// 32-date chunk must survive the chunk's writes.
+// Ring of prefix sums: the h slots behind the oldest new position of an
+// 8-date group must survive the group's writes.
 int ring_len(int n_hist, double h_frac) {
     int hmax = (int)std::floor(h_frac * (double)n_hist);
     if (hmax < 1) hmax = 1;
     if (hmax > n_hist) hmax = n_hist;
-    return hmax + 33;
+    return hmax + 9;
 }
 
 template <int KH, bool kTMA>

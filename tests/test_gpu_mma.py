@@ -82,7 +82,7 @@ def test_mask_bits(bfm):
     _check(w["dates"], w["Y"], g, k=3, n_hist=w["n_hist"], h_frac=w["h_frac"], lam=w["lam"], mask=bits)
 
 
-@pytest.mark.parametrize("k,N,n_hist", [(1, 150, 70), (2, 300, 180), (3, 448, 250)])
+@pytest.mark.parametrize("k,N,n_hist", [(1, 150, 70), (2, 300, 180), (3, 448, 340)])
 def test_harmonics_and_lengths(bfm, k, N, n_hist):
     d, Y, _ = synth.scene(seed=40 + k, m=2048, N=N, n_hist=n_hist, f=23.0, k_gen=k, intercept=0.45,
                           slope=0.0002, coef_umax=0.25, noise_sd=0.03, miss="markov", p_a=0.25, p_b=0.3,
@@ -139,14 +139,14 @@ def test_rounding_noise_only_pixels(bfm):
 
 
 def test_bandwidth_limit_is_refused(bfm):
-    """A bandwidth above 63 observations does not fit the tensor-core form's
+    """A bandwidth above 87 observations does not fit the tensor-core form's
     ring: BFM_EUNSUPPORTED with algo = MMA (AUTO takes the CUDA-core form)."""
-    d, Y, _ = synth.scene(seed=3, m=256, N=448, n_hist=300, f=23.0, k_gen=3, dtype="i16")
+    d, Y, _ = synth.scene(seed=3, m=256, N=448, n_hist=400, f=23.0, k_gen=3, dtype="i16")
     with pytest.raises(bfm.BfmError) as ei:
-        _run(bfm, d, Y, k=3, n_hist=300, h_frac=0.25, lam=1.75)
+        _run(bfm, d, Y, k=3, n_hist=400, h_frac=0.25, lam=1.75)
     assert ei.value.code == 6
-    g = _run(bfm, d, Y, k=3, n_hist=300, h_frac=0.25, lam=1.75, algo=0)
-    _check(d, Y, g, k=3, n_hist=300, h_frac=0.25, lam=1.75, tol=1e-5)
+    g = _run(bfm, d, Y, k=3, n_hist=400, h_frac=0.25, lam=1.75, algo=0)
+    _check(d, Y, g, k=3, n_hist=400, h_frac=0.25, lam=1.75, tol=1e-5)
 
 
 def test_mma_matches_simt_on_same_input(bfm):
