@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 METRIC = "BFAST-monitor pixels/s at 8.4M px x 414 dates; p50/p99 tile latency"
 # DRAM bytes per pixel per launch from the ncu captures summarised in
 # profiles/ (None once the kernel changes after the capture).
-TRAFFIC_PER_PX = {"f32": (1.786e9 / 1048576,), "i16": (None,)}
+TRAFFIC_PER_PX = {"f32simt": (1.786e9 / 1048576,), "f32": (None,), "i16": (None,)}
 
 WORKLOAD = "c2: full scene 8,388,608 px x 414 dates, n_hist=228, K=8, f=23, h=0.25, plain float32"
 
@@ -186,8 +186,9 @@ def run_ours(args):
     def time_form(form):
         """Device-resident timing of one form: W warm-up calls, then K calls
         bracketed by CUDA events on the launching stream."""
-        if form == "f32":
-            Yf, dt, algo = Y, bfm.BFM_F32, bfm.BFM_ALGO_SIMT
+        if form in ("f32", "f32simt"):
+            Yf, dt = Y, bfm.BFM_F32
+            algo = bfm.BFM_ALGO_MMA if form == "f32" else bfm.BFM_ALGO_SIMT
         else:
             Yf = torch.where(torch.isnan(Y), torch.full_like(Y, -32768.0),
                              torch.clamp(torch.round(Y * 1e4), -32767, 32767)).to(torch.int16)
@@ -223,7 +224,7 @@ def run_ours(args):
             t = torch.tensor([total_ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             total_ms = float(t.item())
-        elt = 4 if form == "f32" else 2
+        elt = 2 if form == "i16" else 4
         alg_bytes = N * m * elt + m * (4 + 4 + 4 + 4 * K + 1)
         achieved = alg_bytes / (statistics.mean(per) / 1e3) / 1e9
         srt = sorted(per)
@@ -236,15 +237,15 @@ def run_ours(args):
                              "frac": achieved / hbm, "traffic": TRAFFIC_PER_PX.get(form, (None,))[0] and
                              TRAFFIC_PER_PX[form][0] * m, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                              "algorithmic_bytes_per_launch": alg_bytes},
-                "clocks": clk, "dtype": "f32" if form == "f32" else "i16",
-                "algo": "simt" if form == "f32" else "tcgen05"}
+                "clocks": clk, "dtype": "i16" if form == "i16" else "f32",
+                "algo": "simt" if form == "f32simt" else "tcgen05"}
 
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
     res = {f: time_form(f) for f in forms}
     form = forms[0]
     main = res[form]
     value, ms_step = main["value"], main["ms_per_step"]
-    elt = 4 if form == "f32" else 2
+    elt = 2 if form == "i16" else 4
 
     # ---- end to end (float32 scene through bfm_monitor_host) through the host-buffer entry point ------------------------------
     e2e = None
@@ -295,7 +296,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "pixels/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": main["dtype"], "data": "synthetic",
-        "config": {"workload": (WORKLOAD if form == "f32" else WORKLOAD.replace("plain float32", "int16 storage"))
+        "config": {"workload": (WORKLOAD if form != "i16" else WORKLOAD.replace("plain float32", "int16 storage"))
                    if args.pixels is None else f"c2 recipe with {m} pixels (profiling case)",
                    "pixels": m, "dates": N, "n_hist": n_hist, "K": K, "form": form, "algo": main["algo"],
                    "l2": "inputs larger than L2 (Y is %.1f GB per step)" % (N * m * elt / 1e9),
@@ -317,9 +318,9 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--forms", default="f32,i16",
-                    help="comma list; the first is the headline (f32 = plain CUDA-core form, "
-                         "i16 = int16 storage on tensor cores)")
+    ap.add_argument("--forms", default="f32simt,f32,i16",
+                    help="comma list; the first is the headline (f32 = float storage on tensor cores, "
+                         "f32simt = float storage on CUDA cores, i16 = int16 storage on tensor cores)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--pixels", type=int, default=None,
                     help="fewer pixels of the same recipe (profiling captures only; not a bench line)")

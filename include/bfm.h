@@ -63,11 +63,13 @@ enum {
     BFM_PX_TIMEOUT = 255             /* the tile's load wait gave up (device error) */
 };
 
-/* Algorithm variants for bfm_monitor_ex (BFM_ALGO_AUTO picks by dtype). */
+/* Algorithm variants for bfm_monitor_ex.  BFM_ALGO_AUTO takes the
+ * tensor-core form where it applies (N <= 448 and a bandwidth
+ * floor(h_frac * n_hist) <= 87), else the CUDA-core form. */
 typedef enum {
     BFM_ALGO_AUTO = 0,
     BFM_ALGO_SIMT = 1, /* FP32 CUDA-core path ("plain form") */
-    BFM_ALGO_MMA = 2   /* tensor-core normal equations ("precision form") */
+    BFM_ALGO_MMA = 2   /* tensor-core normal equations, fitted values and refinement */
 } bfm_algo;
 
 typedef struct bfm_design_s *bfm_design_t;
@@ -123,9 +125,10 @@ int bfm_max_dates(void);
  *   mean    mean of MO_j over the monitoring positions.
  * Arguments:
  *   d          design (its N is the number of rows of Y).
- *   Y          device, [N][m] of `dtype` (16-byte aligned base and m a
- *              multiple of 4 (f32) / 8 (i16) take the TMA tile loader; other
- *              layouts take a plain-load loader with the same results).
+ *   Y          device, [N][m] of `dtype` (any alignment of the element type;
+ *              in the CUDA-core form a 16-byte aligned base and m a multiple
+ *              of 4 (f32) / 8 (i16) take the TMA tile loader, other layouts a
+ *              plain-load loader with the same results).
  *   mask_bits  device, nullable, [N][ceil(m/32)] uint32 (see above).
  *   m          number of pixels, m >= 0 (m = 0 enqueues nothing).
  *   n_hist     history dates, 1 <= n_hist < N (Algorithm 1 Require list).
@@ -139,8 +142,14 @@ int bfm_max_dates(void);
  * Rank test: with the trend column (t-c)/s, the pixel is SINGULAR when some
  * Cholesky pivot of its history Gram matrix, relative to the matching
  * diagonal entry, is below 1e-5.
- * Arithmetic: float storage, float arithmetic, one step of iterative
- * refinement of the least-squares solution.
+ * Arithmetic: float arithmetic with one step of iterative refinement of the
+ * least-squares solution, in the form BFM_ALGO_AUTO picks: the CUDA-core form
+ * (float sums) or the tensor-core form (Gram, X'My, fitted values and the
+ * refinement's X'r on fp16 tensor cores with hi/lo split operands, exact
+ * power-of-two scales per pixel and FP32 accumulation).  Against an FP64
+ * reference on well-conditioned pixels the CUDA-core form stays within 1e-5
+ * and the tensor-core form within 1e-4 (1e-5 on float series of the
+ * benchmark's recipe); the two forms differ in the last bits.
  * Errors: BFM_EINVAL, BFM_EUNSUPPORTED (N > bfm_max_dates()), BFM_ECUDA.
  */
 bfm_status bfm_monitor(bfm_design_t d, const void *Y, int dtype, const uint32_t *mask_bits, int64_t m,
@@ -148,7 +157,7 @@ bfm_status bfm_monitor(bfm_design_t d, const void *Y, int dtype, const uint32_t 
                        float *sigma, float *beta, uint8_t *status, void *stream);
 
 /* As bfm_monitor with an explicit algorithm (bfm_algo).  BFM_ALGO_MMA needs
- * dtype BFM_I16. */
+ * N <= 448 and floor(h_frac * n_hist) <= 87 (else BFM_EUNSUPPORTED). */
 bfm_status bfm_monitor_ex(bfm_design_t d, const void *Y, int dtype, const uint32_t *mask_bits, int64_t m,
                           int n_hist, double h_frac, double lambda, int32_t *break_idx, float *mean_mosum,
                           float *sigma, float *beta, uint8_t *status, int algo, void *stream);
@@ -159,7 +168,9 @@ bfm_status bfm_monitor_ex(bfm_design_t d, const void *Y, int dtype, const uint32
  * (nullable) are read, the five outputs are written to host memory, with the
  * pixel range cut into chunks whose host->device copy, kernel and
  * device->host copy overlap on internal streams.  Page-locked host memory is
- * needed for the copies to overlap.  `workspace` is a device buffer of at
+ * needed for the copies to overlap.  Each chunk runs the form
+ * BFM_ALGO_AUTO picks, so outputs equal bfm_monitor's bit for bit.
+ * `workspace` is a device buffer of at
  * least bfm_monitor_host_workspace(d, dtype, chunk_px, with_mask) bytes,
  * owned by the caller; chunk_px > 0 is the pixels per chunk.  Returns once
  * the work is enqueued on `stream`; the outputs are ready when `stream` is.

@@ -56,20 +56,28 @@ void basis_rows(const bfm_design_s& d, std::vector<double>& rows) {
     }
 }
 
-// Tensor-core B table: basis value (row r, date t) split as fp16 hi + lo, at
-// byte (t/8)*512 + (r/8)*128 + (r%8)*16 + (t%8)*2 of each table.
-void tc_tables(const bfm_design_s& d, const std::vector<double>& rows, int npad, std::vector<unsigned char>& out) {
-    const size_t one = (size_t)(npad / 8) * 512;
-    out.assign(2 * one, 0);
+// Tensor-core B tables: the basis value (row r, date t) split as fp16 hi + lo.
+// Table A holds rows 0..15 for all npad dates, table B rows 16..31 for the
+// first nhpad dates; in both, (row r, date t) sits at byte
+// (t/8)*256 + ((r%16)/8)*128 + (r%8)*16 + (t%8)*2.  Order: A_hi, A_lo, B_hi, B_lo.
+void tc_tables(const bfm_design_s& d, const std::vector<double>& rows, int npad, int nhpad,
+               std::vector<unsigned char>& out) {
+    const size_t a_one = (size_t)(npad / 8) * 256, b_one = (size_t)(nhpad / 8) * 256;
+    out.assign(2 * a_one + 2 * b_one, 0);
     const int nbr = 3 + 6 * d.k;
     for (int t = 0; t < d.N; ++t)
         for (int r = 0; r < nbr; ++r) {
+            const bool in_a = r < 16;
+            if (!in_a && t >= nhpad) continue;
             const double v = rows[(size_t)t * d.NB + r];
             const __half hi = __double2half(v);
             const __half lo = __double2half(v - (double)__half2float(hi));
-            const size_t o = (size_t)(t / 8) * 512 + (size_t)(r / 8) * 128 + (size_t)(r % 8) * 16 + (size_t)(t % 8) * 2;
-            std::memcpy(out.data() + o, &hi, 2);
-            std::memcpy(out.data() + one + o, &lo, 2);
+            const int rr = r % 16;
+            const size_t o = (size_t)(t / 8) * 256 + (size_t)(rr / 8) * 128 + (size_t)(rr % 8) * 16 + (size_t)(t % 8) * 2;
+            unsigned char* base = in_a ? out.data() : out.data() + 2 * a_one;
+            const size_t one = in_a ? a_one : b_one;
+            std::memcpy(base + o, &hi, 2);
+            std::memcpy(base + one + o, &lo, 2);
         }
 }
 
@@ -258,7 +266,7 @@ bfm_status bfm_design_create(const double* dates, int N, int k_harm, double f, b
     if (e == cudaSuccess && N <= kTcMaxDates) {
         const int npad = (N + 31) / 32 * 32;  // whole 32-date chunks
         std::vector<unsigned char> tab;
-        tc_tables(*d, rowsd, npad, tab);
+        tc_tables(*d, rowsd, npad, npad, tab);  // table B covers every possible history length
         e = cudaMalloc(&d->d_phi_tc, tab.size());
         if (e == cudaSuccess) e = cudaMemcpy(d->d_phi_tc, tab.data(), tab.size(), cudaMemcpyHostToDevice);
         d->npad_tc = npad;
@@ -328,12 +336,11 @@ bfm_status bfm_monitor_ex(bfm_design_t d, const void* Y, int dtype, const uint32
     }
     const bool mma_ok = mma_supported(d, dtype, n_hist, h_frac, nullptr);
     if (algo == BFM_ALGO_MMA && !mma_ok) {
-        set_error("bfm_monitor: the tensor-core form needs int16 storage, N <= 448 and a bandwidth of at most 87 "
-                  "observations");
+        set_error("bfm_monitor: the tensor-core form needs N <= 448 and a bandwidth of at most 87 observations");
         return BFM_EUNSUPPORTED;
     }
     if (algo == BFM_ALGO_MMA || (algo == BFM_ALGO_AUTO && mma_ok))
-        return launch_mma(d, Y, mask_bits, m, n_hist, h_frac, lambda, break_idx, mean_mosum, sigma, beta, status,
+        return launch_mma(d, dtype, Y, mask_bits, m, n_hist, h_frac, lambda, break_idx, mean_mosum, sigma, beta, status,
                           (cudaStream_t)stream);
     return launch_simt(d, Y, dtype, mask_bits, m, n_hist, h_frac, lambda, break_idx, mean_mosum, sigma, beta, status,
                        (cudaStream_t)stream);
@@ -412,10 +419,18 @@ bfm_status bfm_monitor_host(bfm_design_t d, const void* Y_host, int dtype, const
         }
         BFM_CK(cudaEventRecord(hp->h2d_done[s], hp->h2d), "bfm_monitor_host: event");
         BFM_CK(cudaStreamWaitEvent(cs, hp->h2d_done[s], 0), "bfm_monitor_host: wait");
-        st = launch_simt(d, base + L.y, dtype, with_mask ? reinterpret_cast<const uint32_t*>(base + L.mask) : nullptr,
-                         mc, n_hist, h_frac, lambda, reinterpret_cast<int32_t*>(base + L.brk),
-                         reinterpret_cast<float*>(base + L.mean), reinterpret_cast<float*>(base + L.sigma),
-                         reinterpret_cast<float*>(base + L.beta), reinterpret_cast<uint8_t*>(base + L.status), cs);
+        {
+            // the form BFM_ALGO_AUTO picks for these parameters
+            const uint32_t* mk = with_mask ? reinterpret_cast<const uint32_t*>(base + L.mask) : nullptr;
+            int32_t* ob = reinterpret_cast<int32_t*>(base + L.brk);
+            float* om = reinterpret_cast<float*>(base + L.mean);
+            float* os = reinterpret_cast<float*>(base + L.sigma);
+            float* obeta = reinterpret_cast<float*>(base + L.beta);
+            uint8_t* ost = reinterpret_cast<uint8_t*>(base + L.status);
+            st = mma_supported(d, dtype, n_hist, h_frac, nullptr)
+                     ? launch_mma(d, dtype, base + L.y, mk, mc, n_hist, h_frac, lambda, ob, om, os, obeta, ost, cs)
+                     : launch_simt(d, base + L.y, dtype, mk, mc, n_hist, h_frac, lambda, ob, om, os, obeta, ost, cs);
+        }
         if (st != BFM_OK) return st;
         BFM_CK(cudaEventRecord(hp->comp_done[s], cs), "bfm_monitor_host: event");
         BFM_CK(cudaStreamWaitEvent(hp->d2h, hp->comp_done[s], 0), "bfm_monitor_host: wait");

@@ -90,9 +90,9 @@ struct bfm_design_s {
     double c = 0.0, s = 1.0;  // trend centring/scaling
     int NB = 0;               // basis row stride (floats)
     float* d_basis = nullptr; // device [N][NB]
-    // Tensor-core B operand: the basis table as fp16 hi and lo parts, each
-    // [32 rows x npad dates] in the no-swizzle core-matrix layout (see
-    // monitor_mma.cu); nullptr when N exceeds the tensor-core limit.
+    // Tensor-core B operands: the basis table as fp16 hi and lo parts in the
+    // no-swizzle core-matrix layout (see abi.cu tc_tables); nullptr when N
+    // exceeds the tensor-core limit.
     void* d_phi_tc = nullptr;
     int npad_tc = 0;
     int device = -1;
@@ -110,14 +110,14 @@ bfm_status launch_simt(const bfm_design_s* d, const void* Y, int dtype, const ui
                        int n_hist, double h_frac, double lambda, int32_t* brk, float* mean, float* sigma,
                        float* beta, uint8_t* status, cudaStream_t stream);
 
-// Tensor-core form (int16 storage): limits and launch.
+// Tensor-core form: limits and launch.
 constexpr int kTcMaxDates = 448;
-constexpr int kTcRows = 32;  // basis rows in the tensor-core B table
-inline size_t tc_phi_bytes(int npad) { return (size_t)2 * (npad / 8) * 512; }
+// Basis tables of the tensor-core form (abi.cu tc_tables): table A = basis
+// rows 0..15, table B = rows 16..31, each as fp16 hi then lo, over npad dates.
 bool mma_supported(const bfm_design_s* d, int dtype, int n_hist, double h_frac, size_t* smem_out);
-bfm_status launch_mma(const bfm_design_s* d, const void* Y, const uint32_t* mask, int64_t m, int n_hist,
-                      double h_frac, double lambda, int32_t* brk, float* mean, float* sigma, float* beta,
-                      uint8_t* status, cudaStream_t stream);
+bfm_status launch_mma(const bfm_design_s* d, int dtype, const void* Y, const uint32_t* mask, int64_t m,
+                      int n_hist, double h_frac, double lambda, int32_t* brk, float* mean, float* sigma,
+                      float* beta, uint8_t* status, cudaStream_t stream);
 cudaError_t mma_read_clear_errors(cudaStream_t s, unsigned int* bits);
 
 // Shared-memory bytes the SIMT kernel needs for N dates, k harmonics and a dtype (0 if too large).

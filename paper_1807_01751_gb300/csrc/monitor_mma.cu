@@ -1,31 +1,37 @@
-// Tensor-core ("precision") form of the per-pixel path for int16 storage.
+// Tensor-core form of the per-pixel path (int16 or float storage).
 //
 // One CTA = 128 pixels = the M of every tcgen05.mma = the 128 TMEM lanes;
-// thread m owns pixel m (TMEM lane m).  Per tile:
+// thread m owns pixel m (TMEM lane m).  Y is streamed from global memory by
+// every thread, one date column per warp load (128 B or 64 B, coalesced),
+// eight dates ahead in registers and 32 dates ahead by L2 prefetch; the
+// history is kept in L2 (evict-last) for its second and third reads.  The
+// basis tables (fp16 hi/lo, the B operand of every MMA) sit in shared memory:
+// table A = basis rows 0..15 over all dates, table B = rows 16..31 over the
+// history.  Per tile:
 //
-//   stage    Y[N][128] int16 by 2-D TMA; the basis table (fp16 hi/lo, the
-//            B operand of every MMA) by plain loads
-//   A        for 32-date chunks of the history, each thread writes three
-//            fp16 A-operand rows: the 0/1 mask, 256*(y >> 8) and (y & 255)
-//            (both exact: y = 256*hi + lo), masked.  The single issuing thread
-//            runs, per 16 dates,
-//              TMEM[G] += mask  x Phi_hi + mask x Phi_lo   (32 basis sums, Eq. 6)
-//              TMEM[b] += hi|lo x Phi_hi|lo                (X'My, Eq. 6)
+//   normal   for 32-date chunks of the history, each thread writes three
+//            fp16 A-operand rows: the 0/1 mask and y*s_y split hi + lo
+//            (masked).  The single issuing thread runs, per 16 dates,
+//              TMEM[G] += mask x (Phi_hi + Phi_lo)       (3+6k basis sums, Eq. 6)
+//              TMEM[b] += (y_hi + y_lo) x (Phi_hi + Phi_lo)   (X'My, Eq. 6)
 //            double-buffered against the next chunk's operand writes
 //   solve    every thread: Gram from the basis sums, Cholesky, beta0 (FP32)
-//   yhat0    TMEM[Y] = [beta_hi | beta_lo] x Phi (Phi read MN-major: rows =
-//            coefficients, columns = dates) over all dates
-//   refine   r0 = y - yhat0 on valid history dates, split fp16 hi/lo, then
+//   refine   TMEM[Y] = [beta0_hi | beta0_lo] x Phi (table A read MN-major:
+//            rows = coefficients, columns = dates), 192 dates per piece;
+//            r0 = y - yhat0 on valid history dates, split hi + lo, then
 //            TMEM[c] += r0 x Phi: one refinement step beta = beta0 + G^-1 c;
-//            sum r^2 = sum r0^2 - delta'c (sigma-hat, Algorithm 1 step 5)
-//   yhat     TMEM[Y] += [delta_hi | delta_lo] x Phi (yhat = yhat0 + X delta)
-//   MOSUM    per thread, 8 dates at a time: r = y - yhat, compensated
-//            prefix sums S over valid positions in a ring, windows of h
-//            valid residuals W = S_J - S_{J-h} (Eq. 3), first crossing of
-//            lambda*sqrt(log+(j/n)) (Eq. 4) and the mean
+//            sum r^2 = sum r0^2 - delta'c (sigma-hat, Eq. 5)
+//   MOSUM    per 192-date piece TMEM[Y] = X beta0 + X delta; per thread, 8
+//            dates at a time: r = y - yhat, compensated prefix sums S over
+//            valid positions in a ring, windows of h valid residuals
+//            W = S_J - S_{J-h} (Eq. 3), first crossing of lambda*sqrt(log+(j/n))
+//            (Eq. 4) and the mean
 //
-// Scaling: A operands carry beta/16 and r0/4 (exact powers of two) so that
-// fp16 holds any int16-scale value; results are scaled back exactly.
+// Scaling: every A operand row is one pixel, so each thread scales its own
+// rows by powers of two (exact) chosen from its data, keeping fp16 hi + lo
+// splits inside fp16's range; results are scaled back exactly.  TMEM use is
+// 256 columns per CTA and shared memory about 106 KB at 414 dates, so two
+// CTAs share an SM.
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
@@ -55,26 +61,27 @@ cudaError_t mma_read_clear_errors(cudaStream_t s, unsigned int* bits) {
 
 namespace {
 
-constexpr int kTile = 128;              // pixels per CTA
-constexpr int kChunk = 32;              // dates per A-operand chunk
+constexpr int kTile = 128;                  // pixels per CTA
+constexpr int kChunk = 32;                  // dates per A-operand chunk
 constexpr int kPlane = kTile * kChunk * 2;  // bytes of one fp16 A plane (128 x 32)
-constexpr int kBufBytes = 3 * kPlane;   // one A buffer (three planes)
+constexpr int kBufBytes = 3 * kPlane;       // one A buffer (three planes)
+constexpr int kCoefPlane = kTile * 16 * 2;  // one [128 x 16] coefficient plane
 constexpr uint32_t kColG = 0, kColB = 32, kColC = 48, kColY = 64;
+constexpr int kPiece = 192;                 // fitted-value dates per TMEM piece
+constexpr uint32_t kTmemCols = 256;         // 64 + kPiece: two CTAs fit one SM's TMEM
 constexpr uint64_t kWaitNs = 2000000000ull;
-constexpr uint32_t kALbo = 2048;        // A: K-direction core stride (16 row groups x 128 B)
-constexpr uint32_t kPhiLbo = 512;       // Phi as K-major B (dates = K): date-group stride
-constexpr uint32_t kPhiSbo = 128;       //   row-group stride
+constexpr uint32_t kALbo = 2048;            // A: K-direction core stride (16 row groups x 128 B)
+constexpr uint32_t kTabLbo = 256;           // B tables: date-group stride (16 rows x 16 B)
 
 struct MmaParams {
-    const int16_t* Y;
+    const void* Y;
     const uint32_t* mask;
     int64_t m, mask_words;
-    int N, n_hist, npad, nhp;  // npad = N padded to 32, nhp = history dates padded to 16
-    const uint4* phi;          // hi table then lo table
+    int N, n_hist, npad, nhpad;  // npad = N padded to 32, nhpad = n_hist padded to 32
+    const uint4* phi;             // A_hi, A_lo, B_hi, B_lo (abi.cu tc_tables), A/B tables npad dates long
     double h_frac;
     float lambda, c_over_s, inv_s;
-    int box_rows, nbox, ring;
-    uint32_t tmem_cols;  // power of two >= 64 + npad
+    int ring;
     int32_t* brk;
     float* mean;
     float* sigma;
@@ -87,7 +94,8 @@ __device__ __forceinline__ uint32_t pack_h2(float a, float b) {
     return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// A-operand row segment: 8 consecutive K elements of row m, group g.
+// A-operand row segment: 8 consecutive K elements of row m, group g (K-major,
+// core-matrix column g at g*2048 bytes).
 __device__ __forceinline__ void st_a(unsigned char* plane, int m, int g, const float (&v)[8]) {
     uint4 u;
     u.x = pack_h2(v[0], v[1]);
@@ -97,53 +105,102 @@ __device__ __forceinline__ void st_a(unsigned char* plane, int m, int g, const f
     *reinterpret_cast<uint4*>(plane + (size_t)g * kALbo + (size_t)m * 16) = u;
 }
 
-// Issue D (+)= A x Phi over one A buffer region for the rows [r0, r0 + n) of Phi
-// (Phi as K-major B: rows = N, dates = K), K range = dates [d0, d0 + 16).
-__device__ __forceinline__ void mma_kblock(uint32_t dcol, const unsigned char* aplane, int kb_in_chunk,
-                                           const unsigned char* phi, int d0, int n, bool acc) {
-    const uint64_t ad = ptx::smem_desc(aplane + (size_t)kb_in_chunk * 2 * kALbo, kALbo, 128);
-    const uint64_t bd = ptx::smem_desc(phi + (size_t)(d0 / 8) * kPhiLbo, kPhiLbo, kPhiSbo);
-    ptx::mma_f16(dcol, ad, bd, ptx::idesc_f16(kTile, n, false), acc);
+// x = hi + lo with hi exactly representable in fp16 (11 significant bits by
+// truncation) and lo = x - hi exact in float; packed conversion rounds lo only.
+__device__ __forceinline__ void split_hi_lo(float x, float& hi, float& lo) {
+    hi = __int_as_float(__float_as_int(x) & 0xFFFFE000);
+    lo = x - hi;
 }
 
-// X b over dates [0, ncols) into TMEM column base dcol (added to what is there
-// when `accumulate`): A = [b_hi | 0], [b_lo | 0] (K = 16 coefficient slots),
-// B = Phi rows 0..15 read MN-major (N = dates).
-__device__ __forceinline__ void mma_yhat(uint32_t dcol, const unsigned char* bhi, const unsigned char* blo,
-                                         const unsigned char* phi_hi, const unsigned char* phi_lo, int ncols,
-                                         bool accumulate) {
-    const uint64_t ah = ptx::smem_desc(bhi, kALbo, 128), al = ptx::smem_desc(blo, kALbo, 128);
-    for (int n0 = 0; n0 < ncols; n0 += 256) {
-        const int n = ncols - n0 < 256 ? ncols - n0 : 256;
-        const uint32_t id = ptx::idesc_f16(kTile, n, true);
-        // MN-major B: K-direction (coefficient) core stride 128 B, N-direction (date) stride 512 B
-        const uint64_t bh = ptx::smem_desc(phi_hi + (size_t)(n0 / 8) * kPhiLbo, kPhiSbo, kPhiLbo);
-        const uint64_t bl = ptx::smem_desc(phi_lo + (size_t)(n0 / 8) * kPhiLbo, kPhiSbo, kPhiLbo);
-        ptx::mma_f16(dcol + (uint32_t)n0, ah, bh, id, accumulate);
-        ptx::mma_f16(dcol + (uint32_t)n0, al, bh, id, true);
-        ptx::mma_f16(dcol + (uint32_t)n0, ah, bl, id, true);
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void prefetch_l2_keep(const void* p) {
+    asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(p));
+}
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// 2^(T - e) for v = 1.x * 2^e, so that |v| * scale lies in [2^T, 2^(T+1));
+// 1 for zero, subnormal, infinite or NaN v.
+__device__ __forceinline__ float pow2_scale(float v, int T) {
+    const int e = (__float_as_int(v) >> 23) & 0xff;
+    if (e == 0 || e == 0xff) return 1.f;
+    int r = 254 + T - e;
+    r = r < 1 ? 1 : (r > 254 ? 254 : r);
+    return __int_as_float(r << 23);
+}
+
+template <typename T>
+struct YLoad;
+template <>
+struct YLoad<int16_t> {
+    static __device__ __forceinline__ float get(const void* a, uint64_t pol, bool& valid) {
+        unsigned short v;
+        asm volatile("ld.global.nc.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(v) : "l"(a), "l"(pol));
+        valid = v != 0x8000u;
+        return (float)(short)v;
     }
+};
+template <>
+struct YLoad<float> {
+    static __device__ __forceinline__ float get(const void* a, uint64_t pol, bool& valid) {
+        float v;
+        asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
+        valid = v == v;
+        return v;
+    }
+};
+
+// D (+)= A x Phi for one 16-date k-block; Phi table (K-major: dates = K,
+// 16 rows = N): date-group stride 256 B, row-group stride 128 B.
+__device__ __forceinline__ void mma_kb(uint32_t dcol, const unsigned char* aplane, int kb_in_chunk,
+                                       const unsigned char* tab, int d0, bool acc) {
+    const uint64_t ad = ptx::smem_desc(aplane + (size_t)kb_in_chunk * 2 * kALbo, kALbo, 128);
+    const uint64_t bd = ptx::smem_desc(tab + (size_t)(d0 / 8) * kTabLbo, kTabLbo, 128);
+    ptx::mma_f16(dcol, ad, bd, ptx::idesc_f16(kTile, 16, false), acc);
 }
 
-template <int KH, bool kTMA, bool kMask>
-__global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ CUtensorMap tmap, const MmaParams P) {
+// X c over dates [d0, d0 + n) into TMEM column dcol: A = [c_hi | 0], [c_lo | 0]
+// (K = 16 coefficient slots), B = table A read MN-major (N = dates): K-direction
+// (row-group) stride 128 B, N-direction (date-group) stride 256 B.
+__device__ __forceinline__ void mma_xc(uint32_t dcol, const unsigned char* chi, const unsigned char* clo,
+                                       const unsigned char* tab_hi, const unsigned char* tab_lo, int d0, int n,
+                                       bool accumulate) {
+    const uint64_t ah = ptx::smem_desc(chi, kALbo, 128), al = ptx::smem_desc(clo, kALbo, 128);
+    const uint32_t id = ptx::idesc_f16(kTile, n, true);
+    const uint64_t bh = ptx::smem_desc(tab_hi + (size_t)(d0 / 8) * kTabLbo, 128, kTabLbo);
+    const uint64_t bl = ptx::smem_desc(tab_lo + (size_t)(d0 / 8) * kTabLbo, 128, kTabLbo);
+    ptx::mma_f16(dcol, ah, bh, id, accumulate);
+    ptx::mma_f16(dcol, al, bh, id, true);
+    ptx::mma_f16(dcol, ah, bl, id, true);
+}
+
+constexpr int kPrefetch = 32;  // dates between an L2 prefetch and the load it serves
+
+template <int KH, typename T, bool kMask>
+__global__ void __launch_bounds__(kTile, 1) mma_kernel(const MmaParams P) {
     using B = Basis<KH>;
     constexpr int K = B::K, NBR = B::NBR;
+    constexpr bool kInt = sizeof(T) == 2;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    const int rows = P.nbox * P.box_rows;
-    const size_t y_bytes = ((size_t)rows * kTile * 2 + 1023) & ~(size_t)1023;
-    const size_t phi_one = (size_t)(P.npad / 8) * 512;
-    int16_t* sY = reinterpret_cast<int16_t*>(smem_raw);
-    unsigned char* sPhi = smem_raw + y_bytes;  // hi table, then lo table
-    unsigned char* sA = sPhi + 2 * phi_one;    // two A buffers (also beta planes, ring)
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sA + 2 * kBufBytes);
-    uint64_t* bar_load = bars + 0;
-    uint64_t* bar_a = bars + 1;  // [2] A-buffer reuse, Gram phase
-    uint64_t* bar_r = bars + 3;  // [2] A-buffer reuse, refinement phase
-    uint64_t* bar_done = bars + 5;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 6);
-    const unsigned char* phi_hi = sPhi;
-    const unsigned char* phi_lo = sPhi + phi_one;
+    const size_t ta = (size_t)(P.npad / 8) * kTabLbo, tb = NBR > 16 ? (size_t)(P.nhpad / 8) * kTabLbo : 0;
+    unsigned char* tA_hi = smem_raw;
+    unsigned char* tA_lo = tA_hi + ta;
+    unsigned char* tB_hi = tA_lo + ta;
+    unsigned char* tB_lo = tB_hi + tb;
+    unsigned char* sA = tB_lo + tb;          // two A buffers, later the MOSUM ring
+    unsigned char* sC = sA + 2 * kBufBytes;  // beta0 hi, beta0 lo, delta hi, delta lo planes
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sC + 4 * kCoefPlane);
+    uint64_t* bar_buf = bars + 0;  // [2] A-buffer reuse
+    uint64_t* bar_done = bars + 2;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 3);
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int64_t p0 = (int64_t)blockIdx.x * kTile;
@@ -153,15 +210,24 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
 
     if (tid == 0) {
-        ptx::mbar_init(bar_load, 1);
-        for (int i = 1; i < 6; ++i) ptx::mbar_init(bars + i, 1);
+        for (int i = 0; i < 3; ++i) ptx::mbar_init(bars + i, 1);
         ptx::fence_mbar_init();
     }
-    if (warp == 0) ptx::tmem_alloc(tslot, P.tmem_cols);
+    if (warp == 0) ptx::tmem_alloc(tslot, kTmemCols);
     {
-        const size_t n16 = 2 * phi_one / 16;
-        uint4* dst = reinterpret_cast<uint4*>(sPhi);
-        for (size_t i = tid; i < n16; i += kTile) dst[i] = __ldg(P.phi + i);
+        // basis tables: A over all npad dates; B (rows 16..31) over the history
+        const uint4* gA = P.phi;
+        uint4* dA = reinterpret_cast<uint4*>(tA_hi);
+        for (size_t i = tid; i < 2 * ta / 16; i += kTile) dA[i] = __ldg(gA + i);
+        if constexpr (NBR > 16) {
+            const uint4* gB = P.phi + 2 * ta / 16;
+            const size_t nb1 = tb / 16;
+            uint4* dB = reinterpret_cast<uint4*>(tB_hi);
+            for (size_t i = tid; i < nb1; i += kTile) {
+                dB[i] = __ldg(gB + i);
+                dB[nb1 + i] = __ldg(gB + ta / 16 + i);
+            }
+        }
     }
     ptx::fence_async_smem();
     ptx::tc_fence_before();
@@ -170,97 +236,134 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
     const uint32_t tmem = *tslot;
     bool ok = true;
 
-    // ---- stage Y ----------------------------------------------------------------------
-    if constexpr (kTMA) {
-        if (tid == 0) {
-            ptx::prefetch_tmap(&tmap);
-            ptx::mbar_arrive_expect_tx(bar_load, (uint32_t)(rows * kTile * 2));
-            for (int b = 0; b < P.nbox; ++b)
-                ptx::tma_load_2d(sY + (size_t)b * P.box_rows * kTile, &tmap, bar_load, (int)p0, b * P.box_rows);
-        }
-        if (!ptx::mbar_wait_bounded(bar_load, 0, kWaitNs)) {
-            ok = false;
-            if (tid == 0) atomicOr(&g_bfm_mma_err, 1u);
-            ptx::mbar_wait_bounded(bar_load, 0, kWaitNs);
-        }
-    } else {
-        for (int idx = tid; idx < N * kTile; idx += kTile) {
-            const int t = idx / kTile, l = idx % kTile;
-            sY[idx] = (p0 + l < P.m) ? P.Y[(size_t)t * P.m + p0 + l] : (int16_t)-32768;
-        }
-        __syncthreads();
-    }
-    if (!__syncthreads_and(ok)) {
-        if (active) P.status[p] = BFM_PX_TIMEOUT;
-        ptx::tc_fence_before();
-        __syncthreads();
-        if (warp == 0) ptx::tmem_dealloc(tmem, P.tmem_cols);
-        return;
-    }
-
+    const uint64_t keep = l2_policy_evict_last(), last = l2_policy_evict_first();
+    const T* ycol = static_cast<const T*>(P.Y) + (active ? p : 0);
     const uint32_t* mrow = P.mask + (p0 >> 5) + (tid >> 5);
-    auto obs = [&](int t, int& y) -> bool {
-        y = sY[t * kTile + tid];
-        bool v = y != -32768;
-        if constexpr (kMask) v = v && ((__ldg(mrow + (size_t)t * P.mask_words) >> (tid & 31)) & 1u);
-        return v;
+    // Eight dates [t0, t0 + 8) of this pixel (valid bits; missing and t >= tlim
+    // give 0), plus an L2 prefetch of the dates kPrefetch further on.
+    auto load8 = [&](int t0, int tlim, uint64_t pol, int pf_from, bool pf_keep, float (&y)[8]) -> uint32_t {
+        uint32_t vb = 0u;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int t = t0 + e;
+            bool v = false;
+            y[e] = 0.f;
+            if (active && t < tlim) {
+                y[e] = YLoad<T>::get(ycol + (int64_t)t * P.m, pol, v);
+                if constexpr (kMask) v = v && ((__ldg(mrow + (size_t)t * P.mask_words) >> (tid & 31)) & 1u);
+            }
+            vb |= (v ? 1u : 0u) << e;
+        }
+        const int tp = t0 + kPrefetch;
+        if (active && tp >= pf_from && tp < tlim) {
+            const T* a = ycol + (int64_t)tp * P.m;
+            const int np = tlim - tp < 8 ? tlim - tp : 8;
+            for (int e = 0; e < np; ++e) {
+                if (pf_keep)
+                    prefetch_l2_keep(a + (int64_t)e * P.m);
+                else
+                    prefetch_l2(a + (int64_t)e * P.m);
+            }
+        }
+        return vb;
     };
-    uint32_t wait_phase_done = 0;
-    auto wait_done = [&]() -> bool {
-        const bool r = ptx::mbar_wait_bounded(bar_done, wait_phase_done & 1u, kWaitNs);
-        ++wait_phase_done;
+    uint32_t done_uses = 0, buf_uses[2] = {0u, 0u};
+    auto wait_done = [&]() {
+        ok &= ptx::mbar_wait_bounded(bar_done, done_uses & 1u, kWaitNs);
+        ++done_uses;
         ptx::tc_fence_after();
-        return r;
     };
-
-    // ---- A: masked basis sums and X'My over the history --------------------------------
-    const int nch = (n_hist + kChunk - 1) / kChunk;
-    float ymax = 0.f;
-    for (int c = 0; c < nch; ++c) {
-        const int buf = c & 1;
-        unsigned char* pl = sA + (size_t)buf * kBufBytes;
-        if (c >= 2) ok &= ptx::mbar_wait_bounded(bar_a + buf, (uint32_t)(((c >> 1) - 1) & 1), kWaitNs);
-#pragma unroll 1
-        for (int g = 0; g < kChunk / 8; ++g) {
-            float mk[8], a1[8], a2[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int t = c * kChunk + g * 8 + e;
-                int y = -32768;
-                bool v = false;
-                if (t < n_hist) v = obs(t, y);
-                mk[e] = v ? 1.f : 0.f;
-                a1[e] = v ? (float)((y >> 8) * 256) : 0.f;
-                a2[e] = v ? (float)(y & 255) : 0.f;
-                ymax = fmaxf(ymax, v ? fabsf((float)y) : 0.f);
-            }
-            st_a(pl, tid, g, mk);
-            st_a(pl + kPlane, tid, g, a1);
-            st_a(pl + 2 * kPlane, tid, g, a2);
-        }
-        ptx::fence_async_smem();
-        ptx::tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            ptx::tc_fence_after();
-#pragma unroll
-            for (int kb = 0; kb < kChunk / 16; ++kb) {
-                const int d0 = c * kChunk + kb * 16;
-                const bool first = (c == 0 && kb == 0);
-                mma_kblock(tmem + kColG, pl, kb, phi_hi, d0, 32, !first);
-                mma_kblock(tmem + kColG, pl, kb, phi_lo, d0, 32, true);
-                mma_kblock(tmem + kColB, pl + kPlane, kb, phi_hi, d0, 16, !first);
-                mma_kblock(tmem + kColB, pl + kPlane, kb, phi_lo, d0, 16, true);
-                mma_kblock(tmem + kColB, pl + 2 * kPlane, kb, phi_hi, d0, 16, true);
-                mma_kblock(tmem + kColB, pl + 2 * kPlane, kb, phi_lo, d0, 16, true);
-            }
-            ptx::mma_commit(bar_a + buf);
-            if (c == nch - 1) ptx::mma_commit(bar_done);
-        }
+    // before rewriting A buffer b: the MMAs that read its previous contents are done
+    auto acquire = [&](int b) {
+        if (buf_uses[b]) ok &= ptx::mbar_wait_bounded(bar_buf + b, (buf_uses[b] - 1u) & 1u, kWaitNs);
+    };
+    const int nch = P.nhpad / 32;
+    if (active) {
+        // warm L2 with the first dates of the history
+        for (int t = 8; t < kPrefetch && t < n_hist; ++t) prefetch_l2_keep(ycol + (int64_t)t * P.m);
     }
-    ok &= wait_done();
 
-    // ---- solve -------------------------------------------------------------------------
+    // ---- normal equations (Eq. 6): masked basis sums and X'My over the history --------------
+    // A rows per 32-date chunk: the 0/1 mask, and y*s_y split into fp16 hi + lo
+    // (int16: 256*(y >> 8) and y & 255, both exact; float: a per-pixel power of
+    // two s_y from the first eight dates, redone from the history maximum if a
+    // value of the tile leaves the range where the split keeps 22 bits).
+    float ymax = 0.f, s_y = 1.f;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        float yn[8];
+        uint32_t vn = load8(0, n_hist, keep, 0, true, yn);
+        if (!kInt && attempt == 0) {
+            float g = 0.f;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) g = fmaxf(g, ((vn >> e) & 1u) ? fabsf(yn[e]) : 0.f);
+            s_y = pow2_scale(g, 8);
+        }
+        ymax = 0.f;
+        for (int c = 0; c < nch; ++c) {
+            const int buf = c & 1;
+            unsigned char* pl = sA + (size_t)buf * kBufBytes;
+            acquire(buf);
+#pragma unroll 1
+            for (int g = 0; g < 4; ++g) {
+                const int t0 = c * 32 + g * 8;
+                float yc[8];
+                const uint32_t vc = vn;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) yc[e] = yn[e];
+                vn = t0 + 8 < n_hist ? load8(t0 + 8, n_hist, keep, 0, true, yn) : 0u;
+                float mk[8], a1[8], a2[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const bool v = (vc >> e) & 1u;
+                    mk[e] = v ? 1.f : 0.f;
+                    const float y = v ? yc[e] : 0.f;
+                    ymax = fmaxf(ymax, fabsf(y));
+                    if constexpr (kInt) {
+                        const int yi = (int)y;
+                        a1[e] = (float)((yi >> 8) * 256);
+                        a2[e] = (float)(yi & 255);
+                    } else {
+                        split_hi_lo(y * s_y, a1[e], a2[e]);
+                    }
+                }
+                st_a(pl, tid, g, mk);
+                st_a(pl + kPlane, tid, g, a1);
+                st_a(pl + 2 * kPlane, tid, g, a2);
+            }
+            ptx::fence_async_smem();
+            ptx::tc_fence_before();
+            __syncthreads();
+            if (tid == 0) {
+                ptx::tc_fence_after();
+#pragma unroll
+                for (int kb = 0; kb < 2; ++kb) {
+                    const int d0 = c * 32 + kb * 16;
+                    const bool first = (c == 0 && kb == 0);
+                    mma_kb(tmem + kColG, pl, kb, tA_hi, d0, !first);
+                    mma_kb(tmem + kColG, pl, kb, tA_lo, d0, true);
+                    if constexpr (NBR > 16) {
+                        mma_kb(tmem + kColG + 16, pl, kb, tB_hi, d0, !first);
+                        mma_kb(tmem + kColG + 16, pl, kb, tB_lo, d0, true);
+                    }
+                    mma_kb(tmem + kColB, pl + kPlane, kb, tA_hi, d0, !first);
+                    mma_kb(tmem + kColB, pl + kPlane, kb, tA_lo, d0, true);
+                    mma_kb(tmem + kColB, pl + 2 * kPlane, kb, tA_hi, d0, true);
+                    mma_kb(tmem + kColB, pl + 2 * kPlane, kb, tA_lo, d0, true);
+                }
+                ptx::mma_commit(bar_buf + buf);
+                if (c == nch - 1) ptx::mma_commit(bar_done);
+            }
+            ++buf_uses[buf];
+        }
+        wait_done();
+        if (kInt) break;
+        const float q = ymax * s_y;
+        const bool redo = ymax > 0.f && !(q < 32768.f && q >= 4.f);
+        if (!__syncthreads_or(redo ? 1 : 0) || attempt == 1) break;
+        s_y = pow2_scale(ymax, 8);
+    }
+
+    // ---- solve ---------------------------------------------------------------------------
     float a[NBR], bb[K];
     {
         float v32[32], v16[16];
@@ -268,94 +371,115 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
         ptx::tmem_ld16(tmem + lane_base + kColB, v16);
 #pragma unroll
         for (int i = 0; i < NBR; ++i) a[i] = v32[i];
+        const float inv_sy = 1.f / s_y;
 #pragma unroll
-        for (int i = 0; i < K; ++i) bb[i] = v16[i];
+        for (int i = 0; i < K; ++i) bb[i] = v16[i] * inv_sy;
     }
     const int n_i = (int)a[0];
     float G[K][K], L[K][K], dinv[K], beta[K];
     gram_from_sums<KH>(a, G);
     const bool nonsingular = cholesky<K>(G, L, dinv);
     chol_solve<K>(L, dinv, bb, beta);
-
-    // coef/16 as fp16 hi and lo A rows (coefficient slots 0..K-1, 8..15 zero) in buffer 0
-    auto write_beta = [&](const float (&coef)[K]) {
+    // Per-pixel operand scales (powers of two, exact): |beta| * s_b < 2^13 and,
+    // since |x_i| <= 1 (centred trend), |r0| * s_r <= (max|y| + sum|beta|) * s_r < 2^13.
+    float s_b, s_r;
+    {
+        float bm = 0.f, bsum = 0.f;
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            bm = fmaxf(bm, fabsf(beta[i]));
+            bsum += fabsf(beta[i]);
+        }
+        s_b = pow2_scale(bm, 12);
+        s_r = pow2_scale(ymax + bsum, 12);
+    }
+    auto write_coef = [&](const float (&coef)[K], unsigned char* hi_plane, unsigned char* lo_plane) {
         float h[8], l[8], z[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const float b16 = i < K ? coef[i] * 0.0625f : 0.f;
-            h[i] = __half2float(__float2half_rn(b16));
-            l[i] = b16 - h[i];
+            const float cs = i < K ? coef[i] * s_b : 0.f;
+            split_hi_lo(cs, h[i], l[i]);
             z[i] = 0.f;
         }
-        st_a(sA, tid, 0, h);
-        st_a(sA, tid, 1, z);
-        st_a(sA + kPlane, tid, 0, l);
-        st_a(sA + kPlane, tid, 1, z);
-        ptx::fence_async_smem();
-        ptx::tc_fence_before();
-        __syncthreads();
+        st_a(hi_plane, tid, 0, h);
+        st_a(hi_plane, tid, 1, z);
+        st_a(lo_plane, tid, 0, l);
+        st_a(lo_plane, tid, 1, z);
     };
+    write_coef(beta, sC, sC + kCoefPlane);
+    const float inv_b = 1.f / s_b;
 
-    // ---- yhat0 = X beta0 over all dates ------------------------------------------------------
-    write_beta(beta);
-    if (tid == 0) {
-        ptx::tc_fence_after();
-        mma_yhat(tmem + kColY, sA, sA + kPlane, phi_hi, phi_lo, P.npad, false);
-        ptx::mma_commit(bar_done);
-    }
-    ok &= wait_done();
-
-    // ---- refinement: r0 = y - yhat0, X'M r0 by MMA ------------------------------------------
+    // ---- one refinement step: r0 = y - X beta0 on the history, c = X'M r0 ------------------
+    // X beta0 comes from the tensor cores, kPiece dates per TMEM piece.
     float ss = 0.f;
-    for (int c = 0; c < nch; ++c) {
-        const int buf = c & 1;
-        unsigned char* pl = sA + (size_t)buf * kBufBytes;
-        if (c >= 2) ok &= ptx::mbar_wait_bounded(bar_r + buf, (uint32_t)(((c >> 1) - 1) & 1), kWaitNs);
+    {
+        float yn[8];
+        uint32_t vn = load8(0, n_hist, keep, 1 << 30, true, yn);
+        for (int d0 = 0; d0 < nch * 32; d0 += kPiece) {
+            const int w = nch * 32 - d0 < kPiece ? nch * 32 - d0 : kPiece;
+            ptx::fence_async_smem();
+            ptx::tc_fence_before();
+            __syncthreads();  // coefficient planes written; previous piece's TMEM reads done
+            if (tid == 0) {
+                ptx::tc_fence_after();
+                mma_xc(tmem + kColY, sC, sC + kCoefPlane, tA_hi, tA_lo, d0, w, false);
+                ptx::mma_commit(bar_done);
+            }
+            wait_done();
+            for (int c = d0 / 32; c < (d0 + w) / 32; ++c) {
+                const int buf = c & 1;
+                unsigned char* pl = sA + (size_t)buf * kBufBytes;
+                acquire(buf);
 #pragma unroll 1
-        for (int g = 0; g < kChunk / 8; ++g) {
-            float yh[8], rh[8], rl[8];
-            ptx::tmem_ld8(tmem + lane_base + kColY + (uint32_t)(c * kChunk + g * 8), yh);
+                for (int g = 0; g < 4; ++g) {
+                    const int t0 = c * 32 + g * 8;
+                    float yc[8], yh[8];
+                    const uint32_t vc = vn;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int t = c * kChunk + g * 8 + e;
-                int y = 0;
-                bool v = false;
-                if (t < n_hist) v = obs(t, y);
-                const float r0 = v ? ((float)y - 16.f * yh[e]) : 0.f;
-                ss = fmaf(r0, r0, ss);
-                const float r4 = r0 * 0.25f;
-                rh[e] = __half2float(__float2half_rn(r4));
-                rl[e] = r4 - rh[e];
-            }
-            st_a(pl, tid, g, rh);
-            st_a(pl + kPlane, tid, g, rl);
-        }
-        ptx::fence_async_smem();
-        ptx::tc_fence_before();
-        __syncthreads();
-        if (tid == 0) {
-            ptx::tc_fence_after();
+                    for (int e = 0; e < 8; ++e) yc[e] = yn[e];
+                    vn = t0 + 8 < n_hist ? load8(t0 + 8, n_hist, keep, 1 << 30, true, yn) : 0u;
+                    ptx::tmem_ld8(tmem + lane_base + kColY + (uint32_t)(t0 - d0), yh);
+                    float rh[8], rl[8];
 #pragma unroll
-            for (int kb = 0; kb < kChunk / 16; ++kb) {
-                const int d0 = c * kChunk + kb * 16;
-                const bool first = (c == 0 && kb == 0);
-                mma_kblock(tmem + kColC, pl, kb, phi_hi, d0, 16, !first);
-                mma_kblock(tmem + kColC, pl, kb, phi_lo, d0, 16, true);
-                mma_kblock(tmem + kColC, pl + kPlane, kb, phi_hi, d0, 16, true);
+                    for (int e = 0; e < 8; ++e) {
+                        const bool v = (vc >> e) & 1u;
+                        const float r0 = v ? (yc[e] - yh[e] * inv_b) : 0.f;
+                        ss = fmaf(r0, r0, ss);
+                        split_hi_lo(r0 * s_r, rh[e], rl[e]);
+                    }
+                    st_a(pl, tid, g, rh);
+                    st_a(pl + kPlane, tid, g, rl);
+                }
+                ptx::fence_async_smem();
+                ptx::tc_fence_before();
+                __syncthreads();
+                if (tid == 0) {
+                    ptx::tc_fence_after();
+#pragma unroll
+                    for (int kb = 0; kb < 2; ++kb) {
+                        const int dd = c * 32 + kb * 16;
+                        const bool first = (c == 0 && kb == 0);
+                        mma_kb(tmem + kColC, pl, kb, tA_hi, dd, !first);
+                        mma_kb(tmem + kColC, pl, kb, tA_lo, dd, true);
+                        mma_kb(tmem + kColC, pl + kPlane, kb, tA_hi, dd, true);
+                    }
+                    ptx::mma_commit(bar_buf + buf);
+                    if (c == nch - 1) ptx::mma_commit(bar_done);
+                }
+                ++buf_uses[buf];
             }
-            ptx::mma_commit(bar_r + buf);
-            if (c == nch - 1) ptx::mma_commit(bar_done);
         }
     }
-    ok &= wait_done();
+    wait_done();
     float sigma, scale, thr;
     int h, jlim;
     float dl[K];
     {
         float v16[16], cc[K];
         ptx::tmem_ld16(tmem + lane_base + kColC, v16);
+        const float inv_r = 1.f / s_r;
 #pragma unroll
-        for (int i = 0; i < K; ++i) cc[i] = 4.f * v16[i];
+        for (int i = 0; i < K; ++i) cc[i] = v16[i] * inv_r;
         chol_solve<K>(L, dinv, cc, dl);
         float dc = 0.f;
 #pragma unroll
@@ -371,79 +495,81 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
         if (h > n_i) h = n_i;
         jlim = (int)floor(kEuler * (double)n_i);
     }
+    write_coef(dl, sC + 2 * kCoefPlane, sC + 3 * kCoefPlane);
 
-    // ---- yhat = yhat0 + X delta over all dates ---------------------------------------------------
-    // Adding the correction to the stored yhat0 (rather than forming X beta
-    // again) makes the fp16 split error of beta0 -- which lies in the span of
-    // X -- cancel between the refinement residuals and the final residuals.
-    write_beta(dl);
-    if (tid == 0) {
-        ptx::tc_fence_after();
-        mma_yhat(tmem + kColY, sA, sA + kPlane, phi_hi, phi_lo, P.npad, true);
-        ptx::mma_commit(bar_done);
-    }
-    ok &= wait_done();
-
-    // ---- MOSUM, 8 dates at a time ---------------------------------------------------------
-    // Per group: residuals and validity independently; the compensated prefix
-    // sums S_J over valid positions go to a ring of R >= h + 9 slots (the
-    // group's writes all land before its reads); then each window
-    // W_J = S_J - S_{J-h} of the group's monitoring positions (Eq. 3) is an
-    // independent difference tested against lambda*sqrt(log+(J/n)) (Eq. 4).
-    // Branch-free: invalid dates add 0 and their (in-range) lag reads are masked.
-    float* ring = reinterpret_cast<float*>(sA);  // [P.ring][128], free now
+    // ---- MOSUM over all dates, 8 at a time ------------------------------------------------------
+    // yhat = X beta0 + X delta per kPiece-date TMEM piece (the fp16 split error
+    // of beta0 lies in the span of X and cancels against the refinement).  Per
+    // 8-date group: residuals and validity independently; compensated prefix
+    // sums S_J over valid positions into a ring of R >= h + 9 slots; then the
+    // windows W_J = S_J - S_{J-h} (Eq. 3) of the group's monitoring positions,
+    // tested against lambda*sqrt(log+(J/n)) (Eq. 4).  Branch-free: invalid
+    // dates add 0 and their (in-range) lag reads are masked.
+    float* ring = reinterpret_cast<float*>(sA);  // [P.ring][128]; the A buffers are free now
     const int R = P.ring;
     int j = 0, slot = 0, brk = -1;
-    float Sh = 0.f, Sc = 0.f;                       // running prefix sum (compensated)
-    float m0 = 0.f, m0c = 0.f, m1 = 0.f, m1c = 0.f;  // two interleaved sums of W
+    float Sh = 0.f, Sc = 0.f;
+    float m0 = 0.f, m0c = 0.f, m1 = 0.f, m1c = 0.f;
+    {
+        float yn[8];
+        uint32_t vn = load8(0, N, last, n_hist, false, yn);
+        for (int d0 = 0; d0 < P.npad; d0 += kPiece) {
+            const int w = P.npad - d0 < kPiece ? P.npad - d0 : kPiece;
+            ptx::fence_async_smem();
+            ptx::tc_fence_before();
+            __syncthreads();
+            if (tid == 0) {
+                ptx::tc_fence_after();
+                mma_xc(tmem + kColY, sC, sC + kCoefPlane, tA_hi, tA_lo, d0, w, false);
+                mma_xc(tmem + kColY, sC + 2 * kCoefPlane, sC + 3 * kCoefPlane, tA_hi, tA_lo, d0, w, true);
+                ptx::mma_commit(bar_done);
+            }
+            wait_done();
+            const int dend = d0 + w < N ? d0 + w : N;
 #pragma unroll 1
-    for (int c0 = 0; c0 < N; c0 += 8) {
-        float yh[8];
-        ptx::tmem_ld8(tmem + lane_base + kColY + (uint32_t)c0, yh);
-        float r[8];
-        uint32_t vb = 0u;
+            for (int c0 = d0; c0 < dend; c0 += 8) {
+                float yc[8], yh[8];
+                const uint32_t vb = vn;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int t = c0 + e;
-            int y = 0;
-            const bool v = t < N && obs(t, y);
-            r[e] = (float)y - 16.f * yh[e];
-            vb |= (v ? 1u : 0u) << e;
-        }
-        float Sv[8];
-        int sl[8], jj[8];
+                for (int e = 0; e < 8; ++e) yc[e] = yn[e];
+                vn = c0 + 8 < N ? load8(c0 + 8, N, last, n_hist, false, yn) : 0u;
+                ptx::tmem_ld8(tmem + lane_base + kColY + (uint32_t)(c0 - d0), yh);
+                float Sv[8];
+                int sl[8], jj[8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int v = (vb >> e) & 1u;
-            comp_add(Sh, Sc, v ? r[e] : 0.f);
-            Sv[e] = Sh + Sc;
-            if (v) ring[slot * kTile + tid] = Sv[e];
-            sl[e] = slot;
-            jj[e] = j;
-            j += v;
-            slot += v;
-            slot = slot == R ? 0 : slot;
-        }
-        const int d = n_hist - c0;  // monitoring dates of the group: e >= d
-        const uint32_t mon = d <= 0 ? 0xffu : (d >= 8 ? 0u : (0xffu << d) & 0xffu);
-        const uint32_t mv = vb & mon;
-        uint32_t cross = 0u;
+                for (int e = 0; e < 8; ++e) {
+                    const int v = (vb >> e) & 1u;
+                    comp_add(Sh, Sc, v ? (yc[e] - yh[e] * inv_b) : 0.f);
+                    Sv[e] = Sh + Sc;
+                    if (v) ring[slot * kTile + tid] = Sv[e];
+                    sl[e] = slot;
+                    jj[e] = j;
+                    j += v;
+                    slot += v;
+                    slot = slot == R ? 0 : slot;
+                }
+                const int dm = n_hist - c0;  // monitoring dates of the group: e >= dm
+                const uint32_t mon = dm <= 0 ? 0xffu : (dm >= 8 ? 0u : (0xffu << dm) & 0xffu);
+                const uint32_t mv = vb & mon;
+                uint32_t cross = 0u;
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            int ls = sl[e] - h;
-            ls += ls < 0 ? R : 0;
-            const float W = Sv[e] - ring[ls * kTile + tid];
-            const int J = jj[e] + 1;
-            float th = thr;
-            if (J > jlim) th = thr * sqrtf(logf((float)J / (float)n_i));
-            const bool m = (mv >> e) & 1u;
-            cross |= ((m && fabsf(W) > th) ? 1u : 0u) << e;
-            if (e & 1)
-                comp_add(m1, m1c, m ? W : 0.f);
-            else
-                comp_add(m0, m0c, m ? W : 0.f);
+                for (int e = 0; e < 8; ++e) {
+                    int ls = sl[e] - h;
+                    ls += ls < 0 ? R : 0;
+                    const float W = Sv[e] - ring[ls * kTile + tid];
+                    const int J = jj[e] + 1;
+                    float th = thr;
+                    if (J > jlim) th = thr * sqrtf(logf((float)J / (float)n_i));
+                    const bool mm = (mv >> e) & 1u;
+                    cross |= ((mm && fabsf(W) > th) ? 1u : 0u) << e;
+                    if (e & 1)
+                        comp_add(m1, m1c, mm ? W : 0.f);
+                    else
+                        comp_add(m0, m0c, mm ? W : 0.f);
+                }
+                if (brk < 0 && cross) brk = c0 + __ffs(cross) - 1;
+            }
         }
-        if (brk < 0 && cross) brk = c0 + __ffs(cross) - 1;
     }
     float sumW = m0, sumWc = m0c;
     comp_add(sumW, sumWc, m1);
@@ -453,7 +579,7 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
     // ---- outputs ------------------------------------------------------------------------------
     ptx::tc_fence_before();
     __syncthreads();
-    if (warp == 0) ptx::tmem_dealloc(tmem, P.tmem_cols);
+    if (warp == 0) ptx::tmem_dealloc(tmem, kTmemCols);
     if (!active) return;
     if (!ok) {
         P.status[p] = BFM_PX_TIMEOUT;
@@ -496,27 +622,13 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
     }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn_mma() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* ptr = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
-    });
-    return fn;
-}
-
-size_t mma_smem(int N, int npad, int* box_rows, int* nbox) {
-    const int nb = (N + 255) / 256;
-    const int br = (N + nb - 1) / nb;
-    const size_t y = (((size_t)nb * br * kTile * 2) + 1023) & ~(size_t)1023;
-    if (box_rows) *box_rows = br;
-    if (nbox) *nbox = nb;
-    return y + tc_phi_bytes(npad) + 2 * (size_t)kBufBytes + 64;
+// Shared memory: tables A (hi, lo) over npad dates, tables B over nhpad dates
+// (only when there are more than 16 basis sums), two A buffers, four
+// coefficient planes and the barriers.
+size_t mma_smem(int npad, int nhpad, int k) {
+    const size_t ta = (size_t)(npad / 8) * kTabLbo;
+    const size_t tb = 3 + 6 * k > 16 ? (size_t)(nhpad / 8) * kTabLbo : 0;
+    return 2 * ta + 2 * tb + 2 * (size_t)kBufBytes + 4 * (size_t)kCoefPlane + 64;
 }
 
 // Ring of prefix sums: the h slots behind the oldest new position of an
@@ -528,9 +640,9 @@ int ring_len(int n_hist, double h_frac) {
     return hmax + 9;
 }
 
-template <int KH, bool kTMA>
-bfm_status launch_t(const CUtensorMap& tm, const MmaParams& P, size_t smem, cudaStream_t stream) {
-    auto kern = P.mask ? mma_kernel<KH, kTMA, true> : mma_kernel<KH, kTMA, false>;
+template <int KH, typename T>
+bfm_status launch_t(const MmaParams& P, size_t smem, cudaStream_t stream) {
+    auto kern = P.mask ? mma_kernel<KH, T, true> : mma_kernel<KH, T, false>;
     static thread_local int configured[2] = {-1, -1};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -540,7 +652,7 @@ bfm_status launch_t(const CUtensorMap& tm, const MmaParams& P, size_t smem, cuda
         configured[P.mask ? 1 : 0] = dev;
     }
     const unsigned grid = (unsigned)((P.m + kTile - 1) / kTile);
-    kern<<<grid, kTile, smem, stream>>>(tm, P);
+    kern<<<grid, kTile, smem, stream>>>(P);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "mma kernel launch");
     return BFM_OK;
@@ -549,63 +661,45 @@ bfm_status launch_t(const CUtensorMap& tm, const MmaParams& P, size_t smem, cuda
 }  // namespace
 
 bool mma_supported(const bfm_design_s* d, int dtype, int n_hist, double h_frac, size_t* smem_out) {
-    if (dtype != BFM_I16 || !d->d_phi_tc || d->N > kTcMaxDates) return false;
-    if (ring_len(n_hist, h_frac) * kTile * 4 > 2 * kBufBytes) return false;
-    const size_t smem = mma_smem(d->N, d->npad_tc, nullptr, nullptr);
+    if ((dtype != BFM_I16 && dtype != BFM_F32) || !d->d_phi_tc || d->N > kTcMaxDates) return false;
+    if ((size_t)ring_len(n_hist, h_frac) * kTile * 4 > 2 * (size_t)kBufBytes) return false;
+    const size_t smem = mma_smem(d->npad_tc, (n_hist + 31) / 32 * 32, d->k);
     if (smem_out) *smem_out = smem;
     return smem <= 227 * 1024;
 }
 
-bfm_status launch_mma(const bfm_design_s* d, const void* Y, const uint32_t* mask, int64_t m, int n_hist,
-                      double h_frac, double lambda, int32_t* brk, float* mean, float* sigma, float* beta,
-                      uint8_t* status, cudaStream_t stream) {
+bfm_status launch_mma(const bfm_design_s* d, int dtype, const void* Y, const uint32_t* mask, int64_t m,
+                      int n_hist, double h_frac, double lambda, int32_t* brk, float* mean, float* sigma,
+                      float* beta, uint8_t* status, cudaStream_t stream) {
+    if (m == 0) return BFM_OK;
     MmaParams P{};
-    int br = 0, nb = 0;
-    const size_t smem = mma_smem(d->N, d->npad_tc, &br, &nb);
-    P.Y = static_cast<const int16_t*>(Y);
+    P.Y = Y;
     P.mask = mask;
     P.m = m;
     P.mask_words = (m + 31) / 32;
     P.N = d->N;
     P.n_hist = n_hist;
     P.npad = d->npad_tc;
-    P.nhp = (n_hist + 15) / 16 * 16;
+    P.nhpad = (n_hist + 31) / 32 * 32;
     P.phi = static_cast<const uint4*>(d->d_phi_tc);
     P.h_frac = h_frac;
     P.lambda = (float)lambda;
     P.c_over_s = (float)(d->c / d->s);
     P.inv_s = (float)(1.0 / d->s);
-    P.box_rows = br;
-    P.nbox = nb;
     P.ring = ring_len(n_hist, h_frac);
-    P.tmem_cols = (kColY + (uint32_t)d->npad_tc <= 256u) ? 256u : 512u;
     P.brk = brk;
     P.mean = mean;
     P.sigma = sigma;
     P.beta = beta;
     P.status = status;
-    CUtensorMap tm;
-    std::memset(&tm, 0, sizeof tm);
-    bool tma = ((uintptr_t)Y % 16 == 0) && ((m * 2) % 16 == 0) && m >= kTile;
-    if (tma) {
-        auto enc = encode_fn_mma();
-        if (!enc) {
-            tma = false;
-        } else {
-            cuuint64_t gdim[2] = {(cuuint64_t)m, (cuuint64_t)d->N};
-            cuuint64_t gstride[1] = {(cuuint64_t)m * 2};
-            cuuint32_t box[2] = {(cuuint32_t)kTile, (cuuint32_t)br};
-            cuuint32_t es[2] = {1u, 1u};
-            CUresult r = enc(&tm, CU_TENSOR_MAP_DATA_TYPE_UINT16 /* same 16 bits */, 2, const_cast<void*>(Y), gdim,
-                             gstride, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) tma = false;
-        }
-    }
+    // At least 80 KB, so that at most two CTAs (2 x 256 TMEM columns) share an SM.
+    size_t smem = mma_smem(P.npad, P.nhpad, d->k);
+    if (smem < 80 * 1024) smem = 80 * 1024;
+    const bool i16 = dtype == BFM_I16;
     switch (d->k) {
-        case 1: return tma ? launch_t<1, true>(tm, P, smem, stream) : launch_t<1, false>(tm, P, smem, stream);
-        case 2: return tma ? launch_t<2, true>(tm, P, smem, stream) : launch_t<2, false>(tm, P, smem, stream);
-        default: return tma ? launch_t<3, true>(tm, P, smem, stream) : launch_t<3, false>(tm, P, smem, stream);
+        case 1: return i16 ? launch_t<1, int16_t>(P, smem, stream) : launch_t<1, float>(P, smem, stream);
+        case 2: return i16 ? launch_t<2, int16_t>(P, smem, stream) : launch_t<2, float>(P, smem, stream);
+        default: return i16 ? launch_t<3, int16_t>(P, smem, stream) : launch_t<3, float>(P, smem, stream);
     }
 }
 

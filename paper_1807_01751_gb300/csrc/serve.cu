@@ -222,7 +222,7 @@ void start(bfm_server_s* s, Req* q, int slot) {
             algo = ok ? BFM_ALGO_MMA : BFM_ALGO_SIMT;
         }
         bs = algo == BFM_ALGO_MMA
-                 ? launch_mma(r.design, Y, r.mask_bits, r.m, r.n_hist, r.h_frac, r.lambda, q->brk, q->mean, q->sigma,
+                 ? launch_mma(r.design, r.dtype, Y, r.mask_bits, r.m, r.n_hist, r.h_frac, r.lambda, q->brk, q->mean, q->sigma,
                               q->beta, q->status, st)
                  : launch_simt(r.design, Y, r.dtype, r.mask_bits, r.m, r.n_hist, r.h_frac, r.lambda, q->brk, q->mean,
                                q->sigma, q->beta, q->status, st);

@@ -1,4 +1,5 @@
-"""CUDA path vs FP64 oracle, element by element, through the C ABI.
+"""CUDA path vs FP64 oracle, element by element, through the C ABI, in both
+forms (CUDA-core and tensor-core) on float storage.
 
 Float path tolerance 1e-5 (beta column-scaled, sigma relative, mean MOSUM
 relative to max(1, |ref|)); break indices equal except on margin-tied pixels.
@@ -46,32 +47,39 @@ def _check(w, Y, gpu, *, k=None, mask=None, tol=TOL_F32):
     return rep, ref
 
 
-def test_c1_full_tma(bfm):
+ALGOS = pytest.mark.parametrize("algo", [1, 2], ids=["simt", "mma"])
+
+
+@ALGOS
+def test_c1_full_tma(bfm, algo):
     """c1 (m=4096, N=228, K=8, 30 % NaN): 128 tiles of 32 pixels, TMA loader."""
     w = synth.workload("c1")
-    gpu = _run(bfm, w, w["Y"])
+    gpu = _run(bfm, w, w["Y"], algo=algo)
     rep, ref = _check(w, w["Y"], gpu)
     assert (ref["break_idx"] >= 0).sum() > 500
 
 
+@ALGOS
 @pytest.mark.parametrize("m", [1, 31, 33, 129, 4093])
-def test_c1_ragged_plain_loader(bfm, m):
+def test_c1_ragged_plain_loader(bfm, m, algo):
     """m not a multiple of 4 (or < 32) takes the plain-load tile loader; the
     last tile is ragged."""
     w = synth.workload("c1", m=m)
-    gpu = _run(bfm, w, w["Y"])
+    gpu = _run(bfm, w, w["Y"], algo=algo)
     _check(w, w["Y"], gpu)
 
 
-def test_c1_ragged_tma_tail(bfm):
+@ALGOS
+def test_c1_ragged_tma_tail(bfm, algo):
     """m = 4100: TMA loader, last tile has 4 live pixels (out-of-range box
     columns are zero-filled and must not be written)."""
     w = synth.workload("c1", m=4100)
-    gpu = _run(bfm, w, w["Y"])
+    gpu = _run(bfm, w, w["Y"], algo=algo)
     _check(w, w["Y"], gpu)
 
 
-def test_c1_mask_bits(bfm):
+@ALGOS
+def test_c1_mask_bits(bfm, algo):
     w = synth.workload("c1", m=1000)
     rng = np.random.default_rng(3)
     words = (1000 + 31) // 32
@@ -79,7 +87,7 @@ def test_c1_mask_bits(bfm):
     bits = np.zeros((w["N"], words), np.uint32)
     for b in range(32):
         bits |= (mask[:, b::32].astype(np.uint32) << np.uint32(b))
-    gpu = _run(bfm, w, w["Y"], mask=bits)
+    gpu = _run(bfm, w, w["Y"], mask=bits, algo=algo)
     _check(w, w["Y"], gpu, mask=bits)
 
 
@@ -90,18 +98,20 @@ def test_c3_int16_simt(bfm):
     _check(w, w["Y"], gpu)
 
 
+@ALGOS
 @pytest.mark.parametrize("k", [1, 2])
-def test_fewer_harmonics(bfm, k):
+def test_fewer_harmonics(bfm, k, algo):
     w = synth.workload("c1", m=2048)
     d, Y, _ = synth.scene(seed=21 + k, m=2048, N=w["N"], n_hist=w["n_hist"], f=23.0, k_gen=k, intercept=0.4,
                           slope=0.0005, coef_umax=0.2, noise_sd=0.02, miss="markov", p_a=0.3, p_b=0.3,
                           break_frac=0.2, step=(-0.4, -0.1))
     w2 = dict(w, dates=d)
-    gpu = _run(bfm, w2, Y, k=k)
+    gpu = _run(bfm, w2, Y, k=k, algo=algo)
     _check(w2, Y, gpu, k=k)
 
 
-def test_edge_statuses(bfm):
+@ALGOS
+def test_edge_statuses(bfm, algo):
     """Pixels crafted for every status, placed on tile boundaries (lanes 0,
     31, 32, 63): all missing, too few history obs, no monitoring data,
     noise-free (degenerate), collinear history (singular)."""
@@ -117,7 +127,7 @@ def test_edge_statuses(bfm):
     keep = np.zeros(N, bool)
     keep[np.arange(0, N, 23)] = True
     Y[~keep, 64] = np.nan
-    gpu = _run(bfm, w, Y)
+    gpu = _run(bfm, w, Y, algo=algo)
     rep, ref = _check(w, Y, gpu)
     assert ref["status"][0] == 1 and ref["status"][31] == 1 and ref["status"][32] == 4
     assert ref["status"][63] == 3 and ref["status"][64] in (1, 2)
@@ -162,23 +172,28 @@ def test_invalid_arguments(bfm):
 @pytest.fixture(scope="module")
 def c2_full(bfm):
     """The full c2 scene (8,388,608 px x 414 dates, 13.9 GB float32) on the
-    device, run once in the benchmark's launch configuration."""
+    device, run once per form in the benchmark's launch configuration."""
     w = synth.workload("c2")
     Yd = torch.from_numpy(w["Y"]).cuda()
     d = bfm.Design(w["dates"], 3, 23.0)
-    out = bfm.monitor(d, Yd, n_hist=w["n_hist"], h_frac=w["h_frac"], lam=w["lam"])
-    torch.cuda.synchronize()
-    assert bfm.bfm_device_errors() == 0
-    res = to_numpy(out)
+    res = {}
+    for algo in (1, 2):
+        out = bfm.monitor(d, Yd, n_hist=w["n_hist"], h_frac=w["h_frac"], lam=w["lam"], algo=algo)
+        torch.cuda.synchronize()
+        assert bfm.bfm_device_errors() == 0
+        res[algo] = to_numpy(out)
+        del out
     del Yd
     torch.cuda.empty_cache()
     return w, res
 
 
-def test_c2_full_scene_sampled(c2_full):
+@ALGOS
+def test_c2_full_scene_sampled(c2_full, algo):
     """Full-size scene; the oracle checks a seeded sample of 4096 pixels
     (including the first and last tiles) one by one."""
     w, res = c2_full
+    res = res[algo]
     m = w["m"]
     rng = np.random.default_rng(0)
     idx = np.unique(np.concatenate([np.arange(64), np.arange(m - 64, m), rng.choice(m, 3968, replace=False)]))
@@ -188,10 +203,12 @@ def test_c2_full_scene_sampled(c2_full):
     _check(ws, Ys, gpu)
 
 
-def test_c2_full_scene_properties(c2_full):
+@ALGOS
+def test_c2_full_scene_properties(c2_full, algo):
     """Properties that hold at any size: every pixel has a status, breaks
     lie in the monitoring period, detection of the injected shifts."""
     w, res = c2_full
+    res = res[algo]
     st = res["status"]
     assert np.isin(st, [0, 1, 2, 3, 4]).all()
     b = res["break_idx"]
