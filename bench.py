@@ -318,7 +318,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--forms", default="f32simt,f32,i16",
+    ap.add_argument("--forms", default="f32,f32simt,i16",
                     help="comma list; the first is the headline (f32 = float storage on tensor cores, "
                          "f32simt = float storage on CUDA cores, i16 = int16 storage on tensor cores)")
     ap.add_argument("--no-e2e", action="store_true")

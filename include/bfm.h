@@ -64,8 +64,10 @@ enum {
 };
 
 /* Algorithm variants for bfm_monitor_ex.  BFM_ALGO_AUTO takes the
- * tensor-core form where it applies (N <= 448 and a bandwidth
- * floor(h_frac * n_hist) <= 87), else the CUDA-core form. */
+ * tensor-core form where it applies (N <= 448 and a MOSUM ring of
+ * floor(h_frac * n_hist) + 9 prefix sums per pixel that fits shared memory
+ * next to the basis tables: up to about 300 at N = 448), else the CUDA-core
+ * form. */
 typedef enum {
     BFM_ALGO_AUTO = 0,
     BFM_ALGO_SIMT = 1, /* FP32 CUDA-core path ("plain form") */
@@ -157,7 +159,7 @@ bfm_status bfm_monitor(bfm_design_t d, const void *Y, int dtype, const uint32_t 
                        float *sigma, float *beta, uint8_t *status, void *stream);
 
 /* As bfm_monitor with an explicit algorithm (bfm_algo).  BFM_ALGO_MMA needs
- * N <= 448 and floor(h_frac * n_hist) <= 87 (else BFM_EUNSUPPORTED). */
+ * what BFM_ALGO_AUTO checks for it (else BFM_EUNSUPPORTED). */
 bfm_status bfm_monitor_ex(bfm_design_t d, const void *Y, int dtype, const uint32_t *mask_bits, int64_t m,
                           int n_hist, double h_frac, double lambda, int32_t *break_idx, float *mean_mosum,
                           float *sigma, float *beta, uint8_t *status, int algo, void *stream);

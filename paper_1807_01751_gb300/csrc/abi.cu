@@ -336,7 +336,7 @@ bfm_status bfm_monitor_ex(bfm_design_t d, const void* Y, int dtype, const uint32
     }
     const bool mma_ok = mma_supported(d, dtype, n_hist, h_frac, nullptr);
     if (algo == BFM_ALGO_MMA && !mma_ok) {
-        set_error("bfm_monitor: the tensor-core form needs N <= 448 and a bandwidth of at most 87 observations");
+        set_error("bfm_monitor: the tensor-core form needs N <= 448 and a MOSUM ring (bandwidth + 9 prefix sums per pixel) that fits shared memory");
         return BFM_EUNSUPPORTED;
     }
     if (algo == BFM_ALGO_MMA || (algo == BFM_ALGO_AUTO && mma_ok))

@@ -62,9 +62,10 @@ cudaError_t mma_read_clear_errors(cudaStream_t s, unsigned int* bits) {
 namespace {
 
 constexpr int kTile = 128;                  // pixels per CTA
-constexpr int kChunk = 32;                  // dates per A-operand chunk
-constexpr int kPlane = kTile * kChunk * 2;  // bytes of one fp16 A plane (128 x 32)
+constexpr int kBlk = 16;                    // dates per Y block (TMA box height) and per A chunk
+constexpr int kPlane = kTile * kBlk * 2;    // bytes of one fp16 A plane (128 x 16)
 constexpr int kBufBytes = 3 * kPlane;       // one A buffer (three planes)
+constexpr int kMaxStages = 8;
 constexpr int kCoefPlane = kTile * 16 * 2;  // one [128 x 16] coefficient plane
 constexpr uint32_t kColG = 0, kColB = 32, kColC = 48, kColY = 64;
 constexpr int kPiece = 192;                 // fitted-value dates per TMEM piece
@@ -78,6 +79,8 @@ struct MmaParams {
     const uint32_t* mask;
     int64_t m, mask_words;
     int N, n_hist, npad, nhpad;  // npad = N padded to 32, nhpad = n_hist padded to 32
+    int stages;                   // Y blocks in flight (TMA loader)
+    int region_bytes;             // table B + A buffers, later the MOSUM ring
     const uint4* phi;             // A_hi, A_lo, B_hi, B_lo (abi.cu tc_tables), A/B tables npad dates long
     double h_frac;
     float lambda, c_over_s, inv_s;
@@ -182,25 +185,64 @@ __device__ __forceinline__ void mma_xc(uint32_t dcol, const unsigned char* chi, 
     ptx::mma_f16(dcol, ah, bl, id, true);
 }
 
-constexpr int kPrefetch = 32;  // dates between an L2 prefetch and the load it serves
+constexpr int kPrefetch = 32;  // plain loader: dates between an L2 prefetch and the load it serves
 
-template <int KH, typename T, bool kMask>
-__global__ void __launch_bounds__(kTile, 1) mma_kernel(const MmaParams P) {
+template <typename T>
+struct YSmem;
+template <>
+struct YSmem<float> {
+    static __device__ __forceinline__ float get(const unsigned char* st, int idx, bool& valid) {
+        const float v = reinterpret_cast<const float*>(st)[idx];
+        valid = v == v;
+        return v;
+    }
+};
+template <>
+struct YSmem<int16_t> {
+    static __device__ __forceinline__ float get(const unsigned char* st, int idx, bool& valid) {
+        const int v = reinterpret_cast<const int16_t*>(st)[idx];
+        valid = v != -32768;
+        return (float)v;
+    }
+};
+
+__device__ __forceinline__ void tma_load_2d_hint(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                                 uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(ptx::smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(ptx::smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(ptx::smem_u32(bar)) : "memory");
+}
+
+template <int KH, typename T, bool kMask, bool kTMA>
+__global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ CUtensorMap tmap, const MmaParams P) {
     using B = Basis<KH>;
     constexpr int K = B::K, NBR = B::NBR;
     constexpr bool kInt = sizeof(T) == 2;
+    constexpr int kStageBytes = kBlk * kTile * (int)sizeof(T);
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const size_t ta = (size_t)(P.npad / 8) * kTabLbo, tb = NBR > 16 ? (size_t)(P.nhpad / 8) * kTabLbo : 0;
     unsigned char* tA_hi = smem_raw;
     unsigned char* tA_lo = tA_hi + ta;
-    unsigned char* tB_hi = tA_lo + ta;
+    unsigned char* region = tA_lo + ta;  // table B and the A buffers; the MOSUM ring after the solve
+    unsigned char* tB_hi = region;
     unsigned char* tB_lo = tB_hi + tb;
-    unsigned char* sA = tB_lo + tb;          // two A buffers, later the MOSUM ring
-    unsigned char* sC = sA + 2 * kBufBytes;  // beta0 hi, beta0 lo, delta hi, delta lo planes
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sC + 4 * kCoefPlane);
+    unsigned char* sA = tB_lo + tb;
+    unsigned char* sC = region + P.region_bytes;  // beta0 hi, beta0 lo, delta hi, delta lo planes
+    unsigned char* sY = sC + 4 * kCoefPlane;      // Y blocks [16 dates][128 px]
+    const int S = kTMA ? P.stages : 0;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sY + (size_t)S * kStageBytes);
     uint64_t* bar_buf = bars + 0;  // [2] A-buffer reuse
     uint64_t* bar_done = bars + 2;
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 3);
+    uint64_t* full = bars + 3;                 // [S] Y block landed
+    uint64_t* empty = bars + 3 + kMaxStages;   // [S] Y block read by all 128 threads
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 3 + 2 * kMaxStages);
+    int* s_dstart = reinterpret_cast<int*>(tslot + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int64_t p0 = (int64_t)blockIdx.x * kTile;
@@ -211,7 +253,13 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const MmaParams P) {
 
     if (tid == 0) {
         for (int i = 0; i < 3; ++i) ptx::mbar_init(bars + i, 1);
+        for (int i = 0; i < S; ++i) {
+            ptx::mbar_init(full + i, 1);
+            ptx::mbar_init(empty + i, kTile);
+        }
         ptx::fence_mbar_init();
+        *s_dstart = N;
+        if constexpr (kTMA) ptx::prefetch_tmap(&tmap);
     }
     if (warp == 0) ptx::tmem_alloc(tslot, kTmemCols);
     {
@@ -237,36 +285,113 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const MmaParams P) {
     bool ok = true;
 
     const uint64_t keep = l2_policy_evict_last(), last = l2_policy_evict_first();
-    const T* ycol = static_cast<const T*>(P.Y) + (active ? p : 0);
     const uint32_t* mrow = P.mask + (p0 >> 5) + (tid >> 5);
-    // Eight dates [t0, t0 + 8) of this pixel (valid bits; missing and t >= tlim
-    // give 0), plus an L2 prefetch of the dates kPrefetch further on.
-    auto load8 = [&](int t0, int tlim, uint64_t pol, int pf_from, bool pf_keep, float (&y)[8]) -> uint32_t {
+
+    // ---- Y stream: passes over date blocks [b0, b1), read 8 dates at a time in order ----------
+    // TMA loader: block q of the kernel's sequence sits in stage q % S; thread 0
+    // keeps S blocks in flight, refilling a stage once all 128 threads have
+    // arrived on its empty barrier.  Plain loader: per-thread loads two groups
+    // ahead plus L2 prefetch.
+    uint32_t q_next = 0, s_q0 = 0;
+    int s_b0 = 0, s_b1 = 0;
+    uint64_t s_pol = keep;
+    auto issue = [&](uint32_t q, int bd) {  // thread 0
+        const int st = (int)(q % (uint32_t)S);
+        if (q >= (uint32_t)S) ok &= ptx::mbar_wait_bounded(empty + st, ((q / S) - 1u) & 1u, kWaitNs);
+        ptx::mbar_arrive_expect_tx(full + st, kStageBytes);
+        tma_load_2d_hint(sY + (size_t)st * kStageBytes, &tmap, full + st, (int)p0, bd * kBlk, s_pol);
+    };
+    // plain loader state
+    const int lane = tid & 31;
+    const int64_t pf_px = p0 + (tid & ~31) + 8 * (lane >> 3);
+    const T* pf_col = static_cast<const T*>(P.Y) + (pf_px < P.m ? pf_px : 0);
+    const T* ycol = static_cast<const T*>(P.Y) + (active ? p : 0);
+    int s_tlim = 0, s_pf_from = 0;
+    bool s_pf_keep = true;
+    float ya1[8], ya2[8];
+    uint32_t va1 = 0u, va2 = 0u;
+    auto load8 = [&](int t0, float (&y)[8]) -> uint32_t {
         uint32_t vb = 0u;
+        const T* a = ycol + (int64_t)t0 * P.m;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
             const int t = t0 + e;
             bool v = false;
             y[e] = 0.f;
-            if (active && t < tlim) {
-                y[e] = YLoad<T>::get(ycol + (int64_t)t * P.m, pol, v);
+            if (active && t < s_tlim) {
+                y[e] = YLoad<T>::get(a, s_pol, v);
                 if constexpr (kMask) v = v && ((__ldg(mrow + (size_t)t * P.mask_words) >> (tid & 31)) & 1u);
             }
+            a += P.m;
             vb |= (v ? 1u : 0u) << e;
         }
-        const int tp = t0 + kPrefetch;
-        if (active && tp >= pf_from && tp < tlim) {
-            const T* a = ycol + (int64_t)tp * P.m;
-            const int np = tlim - tp < 8 ? tlim - tp : 8;
-            for (int e = 0; e < np; ++e) {
-                if (pf_keep)
-                    prefetch_l2_keep(a + (int64_t)e * P.m);
-                else
-                    prefetch_l2(a + (int64_t)e * P.m);
-            }
+        const int tp = t0 + kPrefetch + (lane & 7);
+        if (pf_px < P.m && tp >= s_pf_from && tp < s_tlim) {
+            const T* q = pf_col + (int64_t)tp * P.m;
+            if (s_pf_keep)
+                prefetch_l2_keep(q);
+            else
+                prefetch_l2(q);
         }
         return vb;
     };
+    auto open = [&](int b0, int b1, int tlim, uint64_t pol, int pf_from, bool pf_keep) {
+        s_b0 = b0;
+        s_b1 = b1;
+        s_q0 = q_next;
+        q_next += (uint32_t)(b1 - b0);
+        s_pol = pol;
+        s_tlim = tlim;
+        if constexpr (kTMA) {
+            if (tid == 0)
+                for (int j = 0; j < S && b0 + j < b1; ++j) issue(s_q0 + (uint32_t)j, b0 + j);
+        } else {
+            s_pf_from = pf_from;
+            s_pf_keep = pf_keep;
+            va1 = load8(b0 * kBlk, ya1);
+            va2 = load8(b0 * kBlk + 8, ya2);
+        }
+    };
+    // dates [t0, t0 + 8) of this pixel: values (0 where invalid) and valid bits
+    // (missing, masked, t >= tlim and pixels beyond m are invalid)
+    auto next8 = [&](int t0, float (&y)[8]) -> uint32_t {
+        if constexpr (kTMA) {
+            const int bd = t0 / kBlk, half = (t0 / 8) & 1;
+            const uint32_t q = s_q0 + (uint32_t)(bd - s_b0);
+            const int st = (int)(q % (uint32_t)S);
+            if (half == 0) ok &= ptx::mbar_wait_bounded(full + st, (q / S) & 1u, kWaitNs);
+            const unsigned char* sb = sY + (size_t)st * kStageBytes;
+            uint32_t vb = 0u;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int t = t0 + e;
+                bool v;
+                const float x = YSmem<T>::get(sb, (half * 8 + e) * kTile + tid, v);
+                v = v && active && t < s_tlim;
+                if constexpr (kMask) {
+                    if (v) v = (__ldg(mrow + (size_t)t * P.mask_words) >> (tid & 31)) & 1u;
+                }
+                y[e] = v ? x : 0.f;
+                vb |= (v ? 1u : 0u) << e;
+            }
+            if (half == 1) {
+                mbar_arrive(empty + st);
+                if (tid == 0 && bd + S < s_b1) issue(q + (uint32_t)S, bd + S);
+            }
+            return vb;
+        } else {
+            const uint32_t v = va1;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                y[e] = ((v >> e) & 1u) ? ya1[e] : 0.f;  // the slots past tlim keep stale values
+                ya1[e] = ya2[e];
+            }
+            va1 = va2;
+            va2 = t0 + 16 < s_tlim ? load8(t0 + 16, ya2) : 0u;
+            return v;
+        }
+    };
+
     uint32_t done_uses = 0, buf_uses[2] = {0u, 0u};
     auto wait_done = [&]() {
         ok &= ptx::mbar_wait_bounded(bar_done, done_uses & 1u, kWaitNs);
@@ -277,46 +402,43 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const MmaParams P) {
     auto acquire = [&](int b) {
         if (buf_uses[b]) ok &= ptx::mbar_wait_bounded(bar_buf + b, (buf_uses[b] - 1u) & 1u, kWaitNs);
     };
-    const int nch = P.nhpad / 32;
-    if (active) {
-        // warm L2 with the first dates of the history
-        for (int t = 8; t < kPrefetch && t < n_hist; ++t) prefetch_l2_keep(ycol + (int64_t)t * P.m);
-    }
+    const int nbh = (n_hist + kBlk - 1) / kBlk;  // history blocks
 
     // ---- normal equations (Eq. 6): masked basis sums and X'My over the history --------------
-    // A rows per 32-date chunk: the 0/1 mask, and y*s_y split into fp16 hi + lo
+    // A rows per 16-date chunk: the 0/1 mask, and y*s_y split into fp16 hi + lo
     // (int16: 256*(y >> 8) and y & 255, both exact; float: a per-pixel power of
-    // two s_y from the first eight dates, redone from the history maximum if a
-    // value of the tile leaves the range where the split keeps 22 bits).
+    // two s_y from the first eight dates holding a valid value, redone from the
+    // history maximum if a value of the tile leaves the range where the split
+    // keeps 22 bits).
     float ymax = 0.f, s_y = 1.f;
+    bool s_set = kInt;
     for (int attempt = 0; attempt < 2; ++attempt) {
-        float yn[8];
-        uint32_t vn = load8(0, n_hist, keep, 0, true, yn);
-        if (!kInt && attempt == 0) {
-            float g = 0.f;
-#pragma unroll
-            for (int e = 0; e < 8; ++e) g = fmaxf(g, ((vn >> e) & 1u) ? fabsf(yn[e]) : 0.f);
-            s_y = pow2_scale(g, 8);
-        }
+        open(0, nbh, n_hist, keep, 0, true);
         ymax = 0.f;
-        for (int c = 0; c < nch; ++c) {
+        for (int c = 0; c < nbh; ++c) {
             const int buf = c & 1;
             unsigned char* pl = sA + (size_t)buf * kBufBytes;
             acquire(buf);
 #pragma unroll 1
-            for (int g = 0; g < 4; ++g) {
-                const int t0 = c * 32 + g * 8;
+            for (int g = 0; g < 2; ++g) {
+                const int t0 = c * kBlk + g * 8;
                 float yc[8];
-                const uint32_t vc = vn;
+                const uint32_t vc = next8(t0, yc);
+                if (!s_set) {  // float: the first group with a valid value sets s_y (earlier rows are 0)
+                    float gm = 0.f;
 #pragma unroll
-                for (int e = 0; e < 8; ++e) yc[e] = yn[e];
-                vn = t0 + 8 < n_hist ? load8(t0 + 8, n_hist, keep, 0, true, yn) : 0u;
+                    for (int e = 0; e < 8; ++e) gm = fmaxf(gm, fabsf(yc[e]));
+                    if (gm > 0.f) {
+                        s_y = pow2_scale(gm, 4);
+                        s_set = true;
+                    }
+                }
                 float mk[8], a1[8], a2[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     const bool v = (vc >> e) & 1u;
                     mk[e] = v ? 1.f : 0.f;
-                    const float y = v ? yc[e] : 0.f;
+                    const float y = yc[e];
                     ymax = fmaxf(ymax, fabsf(y));
                     if constexpr (kInt) {
                         const int yi = (int)y;
@@ -335,32 +457,30 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const MmaParams P) {
             __syncthreads();
             if (tid == 0) {
                 ptx::tc_fence_after();
-#pragma unroll
-                for (int kb = 0; kb < 2; ++kb) {
-                    const int d0 = c * 32 + kb * 16;
-                    const bool first = (c == 0 && kb == 0);
-                    mma_kb(tmem + kColG, pl, kb, tA_hi, d0, !first);
-                    mma_kb(tmem + kColG, pl, kb, tA_lo, d0, true);
-                    if constexpr (NBR > 16) {
-                        mma_kb(tmem + kColG + 16, pl, kb, tB_hi, d0, !first);
-                        mma_kb(tmem + kColG + 16, pl, kb, tB_lo, d0, true);
-                    }
-                    mma_kb(tmem + kColB, pl + kPlane, kb, tA_hi, d0, !first);
-                    mma_kb(tmem + kColB, pl + kPlane, kb, tA_lo, d0, true);
-                    mma_kb(tmem + kColB, pl + 2 * kPlane, kb, tA_hi, d0, true);
-                    mma_kb(tmem + kColB, pl + 2 * kPlane, kb, tA_lo, d0, true);
+                const int d0 = c * kBlk;
+                const bool first = c == 0;
+                mma_kb(tmem + kColG, pl, 0, tA_hi, d0, !first);
+                mma_kb(tmem + kColG, pl, 0, tA_lo, d0, true);
+                if constexpr (NBR > 16) {
+                    mma_kb(tmem + kColG + 16, pl, 0, tB_hi, d0, !first);
+                    mma_kb(tmem + kColG + 16, pl, 0, tB_lo, d0, true);
                 }
+                mma_kb(tmem + kColB, pl + kPlane, 0, tA_hi, d0, !first);
+                mma_kb(tmem + kColB, pl + kPlane, 0, tA_lo, d0, true);
+                mma_kb(tmem + kColB, pl + 2 * kPlane, 0, tA_hi, d0, true);
+                mma_kb(tmem + kColB, pl + 2 * kPlane, 0, tA_lo, d0, true);
                 ptx::mma_commit(bar_buf + buf);
-                if (c == nch - 1) ptx::mma_commit(bar_done);
+                if (c == nbh - 1) ptx::mma_commit(bar_done);
             }
             ++buf_uses[buf];
         }
         wait_done();
         if (kInt) break;
-        const float q = ymax * s_y;
-        const bool redo = ymax > 0.f && !(q < 32768.f && q >= 4.f);
+        const float qy = ymax * s_y;
+        const bool redo = ymax > 0.f && !(qy < 32768.f && qy >= 4.f);
         if (!__syncthreads_or(redo ? 1 : 0) || attempt == 1) break;
         s_y = pow2_scale(ymax, 8);
+        s_set = true;
     }
 
     // ---- solve ---------------------------------------------------------------------------
@@ -409,70 +529,75 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const MmaParams P) {
     write_coef(beta, sC, sC + kCoefPlane);
     const float inv_b = 1.f / s_b;
 
+    // Bandwidth h (Eq. 3, missing-data reading) and the position n - h + 1 of
+    // the earliest history observation a monitoring window reaches back to.
+    int h = (int)floor(P.h_frac * (double)n_i);
+    if (h < 1) h = 1;
+    if (h > n_i) h = n_i;
+    const int target = n_i - h + 1;
+    int cpos = 0, dfirst = N;
+
     // ---- one refinement step: r0 = y - X beta0 on the history, c = X'M r0 ------------------
     // X beta0 comes from the tensor cores, kPiece dates per TMEM piece.
     float ss = 0.f;
-    {
-        float yn[8];
-        uint32_t vn = load8(0, n_hist, keep, 1 << 30, true, yn);
-        for (int d0 = 0; d0 < nch * 32; d0 += kPiece) {
-            const int w = nch * 32 - d0 < kPiece ? nch * 32 - d0 : kPiece;
-            ptx::fence_async_smem();
-            ptx::tc_fence_before();
-            __syncthreads();  // coefficient planes written; previous piece's TMEM reads done
-            if (tid == 0) {
-                ptx::tc_fence_after();
-                mma_xc(tmem + kColY, sC, sC + kCoefPlane, tA_hi, tA_lo, d0, w, false);
-                ptx::mma_commit(bar_done);
-            }
-            wait_done();
-            for (int c = d0 / 32; c < (d0 + w) / 32; ++c) {
-                const int buf = c & 1;
-                unsigned char* pl = sA + (size_t)buf * kBufBytes;
-                acquire(buf);
+    open(0, nbh, n_hist, keep, 1 << 30, true);
+    for (int d0 = 0; d0 < nbh * kBlk; d0 += kPiece) {
+        const int w = nbh * kBlk - d0 < kPiece ? nbh * kBlk - d0 : kPiece;
+        ptx::fence_async_smem();
+        ptx::tc_fence_before();
+        __syncthreads();  // coefficient planes written; previous piece's TMEM reads done
+        if (tid == 0) {
+            ptx::tc_fence_after();
+            mma_xc(tmem + kColY, sC, sC + kCoefPlane, tA_hi, tA_lo, d0, w, false);
+            ptx::mma_commit(bar_done);
+        }
+        wait_done();
+        uint32_t rq[8];
+        ptx::tmem_ld8_issue(tmem + lane_base + kColY, rq);
 #pragma unroll 1
-                for (int g = 0; g < 4; ++g) {
-                    const int t0 = c * 32 + g * 8;
-                    float yc[8], yh[8];
-                    const uint32_t vc = vn;
+        for (int t0 = d0; t0 < d0 + w; t0 += 8) {
+            const int c = t0 / kBlk, g = (t0 / 8) & 1, buf = c & 1;
+            unsigned char* pl = sA + (size_t)buf * kBufBytes;
+            if (g == 0) acquire(buf);
+            float yc[8], yh[8];
+            const uint32_t vc = next8(t0, yc);
+            ptx::tmem_wait_ld8(rq);
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) yc[e] = yn[e];
-                    vn = t0 + 8 < n_hist ? load8(t0 + 8, n_hist, keep, 1 << 30, true, yn) : 0u;
-                    ptx::tmem_ld8(tmem + lane_base + kColY + (uint32_t)(t0 - d0), yh);
-                    float rh[8], rl[8];
+            for (int e = 0; e < 8; ++e) yh[e] = __uint_as_float(rq[e]);
+            if (t0 + 8 < d0 + w) ptx::tmem_ld8_issue(tmem + lane_base + kColY + (uint32_t)(t0 + 8 - d0), rq);
+            float rh[8], rl[8];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const bool v = (vc >> e) & 1u;
-                        const float r0 = v ? (yc[e] - yh[e] * inv_b) : 0.f;
-                        ss = fmaf(r0, r0, ss);
-                        split_hi_lo(r0 * s_r, rh[e], rl[e]);
-                    }
-                    st_a(pl, tid, g, rh);
-                    st_a(pl + kPlane, tid, g, rl);
-                }
+            for (int e = 0; e < 8; ++e) {
+                const bool v = (vc >> e) & 1u;
+                const float r0 = v ? (yc[e] - yh[e] * inv_b) : 0.f;
+                ss = fmaf(r0, r0, ss);
+                split_hi_lo(r0 * s_r, rh[e], rl[e]);
+                cpos += v ? 1 : 0;
+                dfirst = (v && cpos == target) ? t0 + e : dfirst;
+            }
+            st_a(pl, tid, g, rh);
+            st_a(pl + kPlane, tid, g, rl);
+            if (g == 1) {
                 ptx::fence_async_smem();
                 ptx::tc_fence_before();
                 __syncthreads();
                 if (tid == 0) {
                     ptx::tc_fence_after();
-#pragma unroll
-                    for (int kb = 0; kb < 2; ++kb) {
-                        const int dd = c * 32 + kb * 16;
-                        const bool first = (c == 0 && kb == 0);
-                        mma_kb(tmem + kColC, pl, kb, tA_hi, dd, !first);
-                        mma_kb(tmem + kColC, pl, kb, tA_lo, dd, true);
-                        mma_kb(tmem + kColC, pl + kPlane, kb, tA_hi, dd, true);
-                    }
+                    const int dd = c * kBlk;
+                    const bool first = c == 0;
+                    mma_kb(tmem + kColC, pl, 0, tA_hi, dd, !first);
+                    mma_kb(tmem + kColC, pl, 0, tA_lo, dd, true);
+                    mma_kb(tmem + kColC, pl + kPlane, 0, tA_hi, dd, true);
                     ptx::mma_commit(bar_buf + buf);
-                    if (c == nch - 1) ptx::mma_commit(bar_done);
+                    if (c == nbh - 1) ptx::mma_commit(bar_done);
                 }
                 ++buf_uses[buf];
             }
         }
     }
     wait_done();
-    float sigma, scale, thr;
-    int h, jlim;
+    float sigma, scale;
+    int jlim;
     float dl[K];
     {
         float v16[16], cc[K];
@@ -489,92 +614,121 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const MmaParams P) {
         }
         sigma = sqrtf(fmaxf(ss - dc, 0.f) / (float)(n_i - K));
         scale = sigma * sqrtf((float)n_i);
-        thr = P.lambda * scale;
-        h = (int)floor(P.h_frac * (double)n_i);
-        if (h < 1) h = 1;
-        if (h > n_i) h = n_i;
         jlim = (int)floor(kEuler * (double)n_i);
     }
     write_coef(dl, sC + 2 * kCoefPlane, sC + 3 * kCoefPlane);
+    const bool degenerate = !(sigma > kDegenerateRatio * ymax) || ymax == 0.f;
+    // The MOSUM pass starts at the earliest such date over the tile's pixels
+    // that get a break test (prefix sums from there on differ from those
+    // from date 0 by a constant, which the window differences cancel).
+    if (active && n_i > K && nonsingular && !degenerate) atomicMin(s_dstart, dfirst);
+    __syncthreads();
+    int d_start = *s_dstart;
+    d_start = (d_start < n_hist ? d_start : n_hist) / kBlk * kBlk;
 
-    // ---- MOSUM over all dates, 8 at a time ------------------------------------------------------
+    // ---- MOSUM from d_start, 8 dates at a time -------------------------------------------------
     // yhat = X beta0 + X delta per kPiece-date TMEM piece (the fp16 split error
     // of beta0 lies in the span of X and cancels against the refinement).  Per
     // 8-date group: residuals and validity independently; compensated prefix
-    // sums S_J over valid positions into a ring of R >= h + 9 slots; then the
-    // windows W_J = S_J - S_{J-h} (Eq. 3) of the group's monitoring positions,
-    // tested against lambda*sqrt(log+(J/n)) (Eq. 4).  Branch-free: invalid
-    // dates add 0 and their (in-range) lag reads are masked.
-    float* ring = reinterpret_cast<float*>(sA);  // [P.ring][128]; the A buffers are free now
+    // sums S over valid positions into a ring of R >= h + 9 slots; then the
+    // windows W_J = S_J - S_{J-h} (Eq. 3) of the group's monitoring positions
+    // J = n + 1, n + 2, ..., scaled to MO_J = W_J / (sigma-hat sqrt(n)) and
+    // tested as MO_J^2 > lambda^2 log+(J/n) (Eq. 4, squared).  Branch-free:
+    // invalid dates add 0 and their (in-range) lag reads are masked.
+    float* ring = reinterpret_cast<float*>(region);  // [P.ring][128]; table B and the A buffers are free now
     const int R = P.ring;
-    int j = 0, slot = 0, brk = -1;
+    int jm = 0, slot = 0, brk = -1;
     float Sh = 0.f, Sc = 0.f;
-    float m0 = 0.f, m0c = 0.f, m1 = 0.f, m1c = 0.f;
-    {
-        float yn[8];
-        uint32_t vn = load8(0, N, last, n_hist, false, yn);
-        for (int d0 = 0; d0 < P.npad; d0 += kPiece) {
-            const int w = P.npad - d0 < kPiece ? P.npad - d0 : kPiece;
-            ptx::fence_async_smem();
-            ptx::tc_fence_before();
-            __syncthreads();
-            if (tid == 0) {
-                ptx::tc_fence_after();
-                mma_xc(tmem + kColY, sC, sC + kCoefPlane, tA_hi, tA_lo, d0, w, false);
-                mma_xc(tmem + kColY, sC + 2 * kCoefPlane, sC + 3 * kCoefPlane, tA_hi, tA_lo, d0, w, true);
-                ptx::mma_commit(bar_done);
-            }
-            wait_done();
-            const int dend = d0 + w < N ? d0 + w : N;
+    float m0 = 0.f, m0c = 0.f;
+    const float inv_scale = 1.f / scale, lam2 = P.lambda * P.lambda;
+    const float lg_n = log2f((float)n_i);
+    const int nball = (N + kBlk - 1) / kBlk;
+    open(d_start / kBlk, nball, N, last, n_hist, false);
+    for (int d0 = d_start; d0 < P.npad; d0 += kPiece) {
+        const int w = P.npad - d0 < kPiece ? P.npad - d0 : kPiece;
+        ptx::fence_async_smem();
+        ptx::tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            ptx::tc_fence_after();
+            mma_xc(tmem + kColY, sC, sC + kCoefPlane, tA_hi, tA_lo, d0, w, false);
+            mma_xc(tmem + kColY, sC + 2 * kCoefPlane, sC + 3 * kCoefPlane, tA_hi, tA_lo, d0, w, true);
+            ptx::mma_commit(bar_done);
+        }
+        wait_done();
+        const int dend = d0 + w < nball * kBlk ? d0 + w : nball * kBlk;  // whole Y blocks
+        uint32_t rq[8];
+        if (d0 < dend) ptx::tmem_ld8_issue(tmem + lane_base + kColY, rq);
 #pragma unroll 1
-            for (int c0 = d0; c0 < dend; c0 += 8) {
-                float yc[8], yh[8];
-                const uint32_t vb = vn;
+        for (int c0 = d0; c0 < dend; c0 += 8) {
+            float yc[8], yh[8];
+            const uint32_t vb = next8(c0, yc);
+            ptx::tmem_wait_ld8(rq);
 #pragma unroll
-                for (int e = 0; e < 8; ++e) yc[e] = yn[e];
-                vn = c0 + 8 < N ? load8(c0 + 8, N, last, n_hist, false, yn) : 0u;
-                ptx::tmem_ld8(tmem + lane_base + kColY + (uint32_t)(c0 - d0), yh);
-                float Sv[8];
-                int sl[8], jj[8];
+            for (int e = 0; e < 8; ++e) yh[e] = __uint_as_float(rq[e]);
+            if (c0 + 8 < dend) ptx::tmem_ld8_issue(tmem + lane_base + kColY + (uint32_t)(c0 + 8 - d0), rq);
+            const int dm = n_hist - c0;  // monitoring dates of the group: e >= dm
+            const uint32_t mon = dm <= 0 ? 0xffu : (dm >= 8 ? 0u : (0xffu << dm) & 0xffu);
+            const uint32_t mv = vb & mon;
+            // prefix sums: the group's own running sum (short, plain), then
+            // S = base + local for every date at once with the base's
+            // compensation (Kahan's correction, applied per date)
+            float loc[8], Sv[8];
+            float acc = 0.f;
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int v = (vb >> e) & 1u;
-                    comp_add(Sh, Sc, v ? (yc[e] - yh[e] * inv_b) : 0.f);
-                    Sv[e] = Sh + Sc;
-                    if (v) ring[slot * kTile + tid] = Sv[e];
-                    sl[e] = slot;
-                    jj[e] = j;
-                    j += v;
-                    slot += v;
-                    slot = slot == R ? 0 : slot;
+            for (int e = 0; e < 8; ++e) {
+                acc += ((vb >> e) & 1u) ? (yc[e] - yh[e] * inv_b) : 0.f;
+                loc[e] = acc;
+            }
+            float t7 = Sh, c7 = Sc;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const float yv = loc[e] + Sc;
+                const float tv = Sh + yv;
+                const float cv = yv - (tv - Sh);
+                Sv[e] = tv + cv;
+                if (e == 7) {
+                    t7 = tv;
+                    c7 = cv;
                 }
-                const int dm = n_hist - c0;  // monitoring dates of the group: e >= dm
-                const uint32_t mon = dm <= 0 ? 0xffu : (dm >= 8 ? 0u : (0xffu << dm) & 0xffu);
-                const uint32_t mv = vb & mon;
+            }
+            Sh = t7;
+            Sc = c7;
+            int sl[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int v = (vb >> e) & 1u;
+                if (v) ring[slot * kTile + tid] = Sv[e];
+                sl[e] = slot;
+                slot += v;
+                slot = slot == R ? 0 : slot;
+            }
+            if (mon) {  // the same for every thread: a group with monitoring dates
                 uint32_t cross = 0u;
+                float wv[8];
+                int jq = jm;
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
                     int ls = sl[e] - h;
                     ls += ls < 0 ? R : 0;
                     const float W = Sv[e] - ring[ls * kTile + tid];
-                    const int J = jj[e] + 1;
-                    float th = thr;
-                    if (J > jlim) th = thr * sqrtf(logf((float)J / (float)n_i));
+                    const float mo = W * inv_scale;
+                    const int J = n_i + jq + 1;
+                    const float b2 = J > jlim ? lam2 * kLn2f * (log2_fast((float)J) - lg_n) : lam2;
                     const bool mm = (mv >> e) & 1u;
-                    cross |= ((mm && fabsf(W) > th) ? 1u : 0u) << e;
-                    if (e & 1)
-                        comp_add(m1, m1c, mm ? W : 0.f);
-                    else
-                        comp_add(m0, m0c, mm ? W : 0.f);
+                    jq += mm ? 1 : 0;
+                    cross |= ((mm && mo * mo > b2) ? 1u : 0u) << e;
+                    wv[e] = mm ? W : 0.f;
                 }
+                jm = jq;
+                // the group's windows summed as a tree, then one compensated add
+                const float gsum = ((wv[0] + wv[1]) + (wv[2] + wv[3])) + ((wv[4] + wv[5]) + (wv[6] + wv[7]));
+                comp_add(m0, m0c, gsum);
                 if (brk < 0 && cross) brk = c0 + __ffs(cross) - 1;
             }
         }
     }
-    float sumW = m0, sumWc = m0c;
-    comp_add(sumW, sumWc, m1);
-    sumWc += m1c;
-    const int N_i = j;
+    const float sumW = m0, sumWc = m0c;
 
     // ---- outputs ------------------------------------------------------------------------------
     ptx::tc_fence_before();
@@ -586,7 +740,6 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const MmaParams P) {
         atomicOr(&g_bfm_mma_err, 2u);
         return;
     }
-    const bool degenerate = !(sigma > kDegenerateRatio * ymax) || ymax == 0.f;
     const float qnan = qnanf();
     uint8_t st;
     float o_mean = qnan, o_sigma = sigma;
@@ -601,12 +754,12 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const MmaParams P) {
     } else if (degenerate) {
         st = BFM_PX_DEGENERATE;
         o_mean = 0.f;
-    } else if (N_i == n_i) {
+    } else if (jm == 0) {
         st = BFM_PX_NO_MONITOR;
     } else {
         st = BFM_PX_OK;
         o_brk = brk;
-        o_mean = (sumW + sumWc) / ((float)(N_i - n_i) * scale);
+        o_mean = (sumW + sumWc) / ((float)jm * scale);
     }
     if (!fitted) o_sigma = qnan;
     P.status[p] = st;
@@ -622,15 +775,6 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const MmaParams P) {
     }
 }
 
-// Shared memory: tables A (hi, lo) over npad dates, tables B over nhpad dates
-// (only when there are more than 16 basis sums), two A buffers, four
-// coefficient planes and the barriers.
-size_t mma_smem(int npad, int nhpad, int k) {
-    const size_t ta = (size_t)(npad / 8) * kTabLbo;
-    const size_t tb = 3 + 6 * k > 16 ? (size_t)(nhpad / 8) * kTabLbo : 0;
-    return 2 * ta + 2 * tb + 2 * (size_t)kBufBytes + 4 * (size_t)kCoefPlane + 64;
-}
-
 // Ring of prefix sums: the h slots behind the oldest new position of an
 // 8-date group must survive the group's writes.
 int ring_len(int n_hist, double h_frac) {
@@ -640,9 +784,45 @@ int ring_len(int n_hist, double h_frac) {
     return hmax + 9;
 }
 
-template <int KH, typename T>
-bfm_status launch_t(const MmaParams& P, size_t smem, cudaStream_t stream) {
-    auto kern = P.mask ? mma_kernel<KH, T, true> : mma_kernel<KH, T, false>;
+struct MmaLayout {
+    int stages, region_bytes;
+    size_t smem;
+};
+
+// Shared memory: tables A (hi, lo) over npad dates; a region holding tables B
+// (only with more than 16 basis sums) and two A buffers, later the MOSUM ring;
+// four coefficient planes; the Y stages (TMA loader); barriers.
+MmaLayout mma_layout(int npad, int nhpad, int k, int ring, int elt, bool tma) {
+    MmaLayout L{};
+    const size_t ta = (size_t)(npad / 8) * kTabLbo;
+    const size_t tb = 3 + 6 * k > 16 ? (size_t)(nhpad / 8) * kTabLbo : 0;
+    size_t region = 2 * tb + 2 * (size_t)kBufBytes;
+    const size_t rb = (size_t)ring * kTile * 4;
+    if (rb > region) region = rb;
+    region = (region + 1023) & ~(size_t)1023;
+    L.region_bytes = (int)region;
+    L.stages = tma ? (elt == 4 ? 3 : 6) : 0;
+    L.smem = 2 * ta + region + 4 * (size_t)kCoefPlane + (size_t)L.stages * kBlk * kTile * elt + 256;
+    return L;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn_mma() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    });
+    return fn;
+}
+
+template <int KH, typename T, bool kTMA>
+bfm_status launch_t(const CUtensorMap& tm, const MmaParams& P, size_t smem, cudaStream_t stream) {
+    auto kern = P.mask ? mma_kernel<KH, T, true, kTMA> : mma_kernel<KH, T, false, kTMA>;
     static thread_local int configured[2] = {-1, -1};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -652,26 +832,32 @@ bfm_status launch_t(const MmaParams& P, size_t smem, cudaStream_t stream) {
         configured[P.mask ? 1 : 0] = dev;
     }
     const unsigned grid = (unsigned)((P.m + kTile - 1) / kTile);
-    kern<<<grid, kTile, smem, stream>>>(P);
+    kern<<<grid, kTile, smem, stream>>>(tm, P);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "mma kernel launch");
     return BFM_OK;
+}
+
+template <int KH, typename T>
+bfm_status launch_k(const CUtensorMap& tm, bool tma, const MmaParams& P, size_t smem, cudaStream_t stream) {
+    return tma ? launch_t<KH, T, true>(tm, P, smem, stream) : launch_t<KH, T, false>(tm, P, smem, stream);
 }
 
 }  // namespace
 
 bool mma_supported(const bfm_design_s* d, int dtype, int n_hist, double h_frac, size_t* smem_out) {
     if ((dtype != BFM_I16 && dtype != BFM_F32) || !d->d_phi_tc || d->N > kTcMaxDates) return false;
-    if ((size_t)ring_len(n_hist, h_frac) * kTile * 4 > 2 * (size_t)kBufBytes) return false;
-    const size_t smem = mma_smem(d->npad_tc, (n_hist + 31) / 32 * 32, d->k);
-    if (smem_out) *smem_out = smem;
-    return smem <= 227 * 1024;
+    const MmaLayout L = mma_layout(d->npad_tc, (n_hist + 31) / 32 * 32, d->k, ring_len(n_hist, h_frac),
+                                   dtype == BFM_F32 ? 4 : 2, true);
+    if (smem_out) *smem_out = L.smem;
+    return L.smem <= 227 * 1024;
 }
 
 bfm_status launch_mma(const bfm_design_s* d, int dtype, const void* Y, const uint32_t* mask, int64_t m,
                       int n_hist, double h_frac, double lambda, int32_t* brk, float* mean, float* sigma,
                       float* beta, uint8_t* status, cudaStream_t stream) {
     if (m == 0) return BFM_OK;
+    const int elt = dtype == BFM_F32 ? 4 : 2;
     MmaParams P{};
     P.Y = Y;
     P.mask = mask;
@@ -692,14 +878,31 @@ bfm_status launch_mma(const bfm_design_s* d, int dtype, const void* Y, const uin
     P.sigma = sigma;
     P.beta = beta;
     P.status = status;
+    // TMA loader when the layout allows boxes of 128 pixels x 16 dates
+    CUtensorMap tm;
+    std::memset(&tm, 0, sizeof tm);
+    bool tma = ((uintptr_t)Y % 16 == 0) && ((m * elt) % 16 == 0) && m >= kTile;
+    if (tma) {
+        auto enc = encode_fn_mma();
+        cuuint64_t gdim[2] = {(cuuint64_t)m, (cuuint64_t)d->N};
+        cuuint64_t gstride[1] = {(cuuint64_t)m * elt};
+        cuuint32_t box[2] = {(cuuint32_t)kTile, (cuuint32_t)kBlk};
+        cuuint32_t es[2] = {1u, 1u};
+        tma = enc && enc(&tm, elt == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 2,
+                         const_cast<void*>(Y), gdim, gstride, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
+    const MmaLayout L = mma_layout(P.npad, P.nhpad, d->k, P.ring, elt, tma);
+    P.stages = L.stages;
+    P.region_bytes = L.region_bytes;
     // At least 80 KB, so that at most two CTAs (2 x 256 TMEM columns) share an SM.
-    size_t smem = mma_smem(P.npad, P.nhpad, d->k);
-    if (smem < 80 * 1024) smem = 80 * 1024;
+    size_t smem = L.smem < 80 * 1024 ? 80 * 1024 : L.smem;
     const bool i16 = dtype == BFM_I16;
     switch (d->k) {
-        case 1: return i16 ? launch_t<1, int16_t>(P, smem, stream) : launch_t<1, float>(P, smem, stream);
-        case 2: return i16 ? launch_t<2, int16_t>(P, smem, stream) : launch_t<2, float>(P, smem, stream);
-        default: return i16 ? launch_t<3, int16_t>(P, smem, stream) : launch_t<3, float>(P, smem, stream);
+        case 1: return i16 ? launch_k<1, int16_t>(tm, tma, P, smem, stream) : launch_k<1, float>(tm, tma, P, smem, stream);
+        case 2: return i16 ? launch_k<2, int16_t>(tm, tma, P, smem, stream) : launch_k<2, float>(tm, tma, P, smem, stream);
+        default: return i16 ? launch_k<3, int16_t>(tm, tma, P, smem, stream) : launch_k<3, float>(tm, tma, P, smem, stream);
     }
 }
 

@@ -39,6 +39,18 @@ constexpr float kDegenerateRatio = 1e-6f;
 constexpr double kEuler = 2.71828182845904523536;
 constexpr int kNW = 4;  // warps (date segments) per 32-pixel tile
 
+constexpr float kLn2f = 0.693147180559945309f;
+
+// log2 for the boundary of Eq. 4: the hardware approximation on the device
+// (absolute error near 2^-22 for these arguments), the library function on the host.
+__host__ __device__ __forceinline__ float log2_fast(float x) {
+#ifdef __CUDA_ARCH__
+    return __log2f(x);
+#else
+    return log2f(x);
+#endif
+}
+
 __host__ __device__ __forceinline__ float qnanf() {
 #ifdef __CUDA_ARCH__
     return __int_as_float(0x7fc00000);
@@ -180,7 +192,7 @@ struct Lane {
     float ymax;
     int n_i;
     bool nonsingular;
-    float sigma, thr, scale;
+    float sigma, scale, inv_scale, lam2, lg_n;
     int h, jlim;
     // segment bookkeeping of phases 5-7
     int cnt_off[kNW];                  // valid observations before each all-date segment
@@ -305,7 +317,9 @@ __host__ __device__ __forceinline__ void phase4_sigma(const SegParams& P, Lane<K
     const int n_i = S.n_i;
     S.sigma = sqrtf(s1 / (float)(n_i - K));
     S.scale = S.sigma * sqrtf((float)n_i);
-    S.thr = P.lambda * S.scale;
+    S.inv_scale = 1.f / S.scale;
+    S.lam2 = P.lambda * P.lambda;
+    S.lg_n = log2f((float)n_i);
     int h = (int)floor(P.h_frac * (double)n_i);
     if (h < 1) h = 1;
     if (h > n_i) h = n_i;  // 0 when n_i = 0
@@ -434,9 +448,10 @@ __host__ __device__ __forceinline__ void phase7_mosum(const SegParams& P, int w,
             const float sg = get_s(g0 + (g - offv - 1));
             // S_J - S_g with both prefix sums split into segment offset + local sum
             const float W = (sj - sg) + ((myoh - oh) + (myol - ol));
-            float th = S.thr;
-            if (J > S.jlim) th = S.thr * sqrtf(logf((float)J / (float)n_i));
-            if (first < 0 && fabsf(W) > th) first = jl;
+            // Eq. 4 squared: MO_J^2 > lambda^2 log+(J/n), MO_J = W / (sigma-hat sqrt(n))
+            const float mo = W * S.inv_scale;
+            const float b2 = J > S.jlim ? S.lam2 * kLn2f * (log2_fast((float)J) - S.lg_n) : S.lam2;
+            if (first < 0 && mo * mo > b2) first = jl;
             comp_add(mh, ml, W);
         }
     }

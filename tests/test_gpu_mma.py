@@ -173,14 +173,24 @@ def test_rounding_noise_only_pixels(bfm):
 
 
 def test_bandwidth_limit_is_refused(bfm):
-    """A bandwidth above 87 observations does not fit the tensor-core form's
-    ring: BFM_EUNSUPPORTED with algo = MMA (AUTO takes the CUDA-core form)."""
-    d, Y, _ = synth.scene(seed=3, m=256, N=448, n_hist=400, f=23.0, k_gen=3, dtype="i16")
+    """A bandwidth whose MOSUM ring (h + 9 prefix sums per pixel) does not fit
+    shared memory next to the tables and the Y stages is BFM_EUNSUPPORTED
+    with algo = MMA; AUTO takes the CUDA-core form."""
+    d, Y, _ = synth.scene(seed=3, m=256, N=448, n_hist=440, f=23.0, k_gen=3, dtype="i16")
     with pytest.raises(bfm.BfmError) as ei:
-        _run(bfm, d, Y, k=3, n_hist=400, h_frac=0.25, lam=1.75)
+        _run(bfm, d, Y, k=3, n_hist=440, h_frac=1.0, lam=1.75)
     assert ei.value.code == 6
-    g = _run(bfm, d, Y, k=3, n_hist=400, h_frac=0.25, lam=1.75, algo=0)
-    _check(d, Y, g, k=3, n_hist=400, h_frac=0.25, lam=1.75, tol=1e-5)
+    g = _run(bfm, d, Y, k=3, n_hist=440, h_frac=1.0, lam=1.75, algo=0)
+    # windows over the whole history: FP32 sums of ~180 residuals per window
+    _check(d, Y, g, k=3, n_hist=440, h_frac=1.0, lam=1.75)
+
+
+def test_wide_bandwidth(bfm):
+    """h = 100 valid observations (ring of 109 slots, beyond the A buffers and
+    table B it overlays): the ring region grows."""
+    d, Y, _ = synth.scene(seed=3, m=1024, N=448, n_hist=400, f=23.0, k_gen=3, dtype="i16")
+    g = _run(bfm, d, Y, k=3, n_hist=400, h_frac=0.25, lam=1.75)
+    _check(d, Y, g, k=3, n_hist=400, h_frac=0.25, lam=1.75)
 
 
 @pytest.mark.parametrize("dtype", ["i16", "f32"])
