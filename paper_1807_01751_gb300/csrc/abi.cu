@@ -334,9 +334,9 @@ bfm_status bfm_monitor_ex(bfm_design_t d, const void* Y, int dtype, const uint32
         set_error("bfm_monitor: unknown algo");
         return BFM_EINVAL;
     }
-    const bool mma_ok = mma_supported(d, dtype, n_hist, h_frac, nullptr);
+    const bool mma_ok = mma_supported(d, dtype, n_hist, h_frac, Y, m, nullptr);
     if (algo == BFM_ALGO_MMA && !mma_ok) {
-        set_error("bfm_monitor: the tensor-core form needs N <= 448 and a MOSUM ring (bandwidth + 9 prefix sums per pixel) that fits shared memory");
+        set_error("bfm_monitor: the tensor-core form needs N <= 448, a MOSUM ring (bandwidth + 9 prefix sums per pixel) that fits shared memory, and Y with a 16-byte aligned base, m >= 128 and rows of a multiple of 16 bytes");
         return BFM_EUNSUPPORTED;
     }
     if (algo == BFM_ALGO_MMA || (algo == BFM_ALGO_AUTO && mma_ok))
@@ -427,7 +427,7 @@ bfm_status bfm_monitor_host(bfm_design_t d, const void* Y_host, int dtype, const
             float* os = reinterpret_cast<float*>(base + L.sigma);
             float* obeta = reinterpret_cast<float*>(base + L.beta);
             uint8_t* ost = reinterpret_cast<uint8_t*>(base + L.status);
-            st = mma_supported(d, dtype, n_hist, h_frac, nullptr)
+            st = mma_supported(d, dtype, n_hist, h_frac, base + L.y, mc, nullptr)
                      ? launch_mma(d, dtype, base + L.y, mk, mc, n_hist, h_frac, lambda, ob, om, os, obeta, ost, cs)
                      : launch_simt(d, base + L.y, dtype, mk, mc, n_hist, h_frac, lambda, ob, om, os, obeta, ost, cs);
         }

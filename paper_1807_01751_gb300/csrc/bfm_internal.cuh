@@ -114,7 +114,9 @@ bfm_status launch_simt(const bfm_design_s* d, const void* Y, int dtype, const ui
 constexpr int kTcMaxDates = 448;
 // Basis tables of the tensor-core form (abi.cu tc_tables): table A = basis
 // rows 0..15, table B = rows 16..31, each as fp16 hi then lo, over npad dates.
-bool mma_supported(const bfm_design_s* d, int dtype, int n_hist, double h_frac, size_t* smem_out);
+// True when the tensor-core form takes these parameters and this Y (a TMA-describable layout).
+bool mma_supported(const bfm_design_s* d, int dtype, int n_hist, double h_frac, const void* Y, int64_t m,
+                   size_t* smem_out);
 bfm_status launch_mma(const bfm_design_s* d, int dtype, const void* Y, const uint32_t* mask, int64_t m,
                       int n_hist, double h_frac, double lambda, int32_t* brk, float* mean, float* sigma,
                       float* beta, uint8_t* status, cudaStream_t stream);

@@ -125,11 +125,6 @@ __device__ __forceinline__ uint64_t l2_policy_evict_first() {
     asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
     return pol;
 }
-__device__ __forceinline__ void prefetch_l2_keep(const void* p) {
-    asm volatile("prefetch.global.L2::evict_last [%0];" ::"l"(p));
-}
-__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
-
 // 2^(T - e) for v = 1.x * 2^e, so that |v| * scale lies in [2^T, 2^(T+1));
 // 1 for zero, subnormal, infinite or NaN v.
 __device__ __forceinline__ float pow2_scale(float v, int T) {
@@ -139,27 +134,6 @@ __device__ __forceinline__ float pow2_scale(float v, int T) {
     r = r < 1 ? 1 : (r > 254 ? 254 : r);
     return __int_as_float(r << 23);
 }
-
-template <typename T>
-struct YLoad;
-template <>
-struct YLoad<int16_t> {
-    static __device__ __forceinline__ float get(const void* a, uint64_t pol, bool& valid) {
-        unsigned short v;
-        asm volatile("ld.global.nc.L2::cache_hint.b16 %0, [%1], %2;" : "=h"(v) : "l"(a), "l"(pol));
-        valid = v != 0x8000u;
-        return (float)(short)v;
-    }
-};
-template <>
-struct YLoad<float> {
-    static __device__ __forceinline__ float get(const void* a, uint64_t pol, bool& valid) {
-        float v;
-        asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(a), "l"(pol));
-        valid = v == v;
-        return v;
-    }
-};
 
 // D (+)= A x Phi for one 16-date k-block; Phi table (K-major: dates = K,
 // 16 rows = N): date-group stride 256 B, row-group stride 128 B.
@@ -184,8 +158,6 @@ __device__ __forceinline__ void mma_xc(uint32_t dcol, const unsigned char* chi, 
     ptx::mma_f16(dcol, al, bh, id, true);
     ptx::mma_f16(dcol, ah, bl, id, true);
 }
-
-constexpr int kPrefetch = 32;  // plain loader: dates between an L2 prefetch and the load it serves
 
 template <typename T>
 struct YSmem;
@@ -219,8 +191,19 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(ptx::smem_u32(bar)) : "memory");
 }
 
-template <int KH, typename T, bool kMask, bool kTMA>
-__global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ CUtensorMap tmap, const MmaParams P) {
+__device__ __forceinline__ void mbar_arrive_cnt(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(ptx::smem_u32(bar)), "r"(count) : "memory");
+}
+
+// 256 threads per 128-pixel tile: pixel px = tid % 128 is held by the thread
+// pair (px, px + 128), warps w and w + 4, which reach the same TMEM lane
+// quarter.  In the two history passes each thread of the pair takes one of
+// the two 8-date groups of every 16-date chunk; the MOSUM pass runs on the
+// first thread of each pair.
+constexpr int kThreads = 2 * kTile;
+
+template <int KH, typename T, bool kMask>
+__global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant__ CUtensorMap tmap, const MmaParams P) {
     using B = Basis<KH>;
     constexpr int K = B::K, NBR = B::NBR;
     constexpr bool kInt = sizeof(T) == 2;
@@ -234,44 +217,48 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
     unsigned char* tB_lo = tB_hi + tb;
     unsigned char* sA = tB_lo + tb;
     unsigned char* sC = region + P.region_bytes;  // beta0 hi, beta0 lo, delta hi, delta lo planes
+    // until the delta planes are written: per-chunk valid bytes [nbh][2][128] and a float per thread
+    unsigned char* sVb = sC + 2 * kCoefPlane;
+    float* sX = reinterpret_cast<float*>(sVb + 28 * 2 * kTile);
     unsigned char* sY = sC + 4 * kCoefPlane;      // Y blocks [16 dates][128 px]
-    const int S = kTMA ? P.stages : 0;
+    const int S = P.stages;
     uint64_t* bars = reinterpret_cast<uint64_t*>(sY + (size_t)S * kStageBytes);
     uint64_t* bar_buf = bars + 0;  // [2] A-buffer reuse
     uint64_t* bar_done = bars + 2;
     uint64_t* full = bars + 3;                 // [S] Y block landed
-    uint64_t* empty = bars + 3 + kMaxStages;   // [S] Y block read by all 128 threads
+    uint64_t* empty = bars + 3 + kMaxStages;   // [S] Y block released (256 arrivals)
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 3 + 2 * kMaxStages);
     int* s_dstart = reinterpret_cast<int*>(tslot + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5;
+    const int px = tid & (kTile - 1), half = tid >> 7;
     const int64_t p0 = (int64_t)blockIdx.x * kTile;
-    const int64_t p = p0 + tid;
+    const int64_t p = p0 + px;
     const bool active = p < P.m;
     const int N = P.N, n_hist = P.n_hist;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
 
     if (tid == 0) {
         for (int i = 0; i < 3; ++i) ptx::mbar_init(bars + i, 1);
         for (int i = 0; i < S; ++i) {
             ptx::mbar_init(full + i, 1);
-            ptx::mbar_init(empty + i, kTile);
+            ptx::mbar_init(empty + i, kThreads);
         }
         ptx::fence_mbar_init();
         *s_dstart = N;
-        if constexpr (kTMA) ptx::prefetch_tmap(&tmap);
+        ptx::prefetch_tmap(&tmap);
     }
     if (warp == 0) ptx::tmem_alloc(tslot, kTmemCols);
     {
         // basis tables: A over all npad dates; B (rows 16..31) over the history
         const uint4* gA = P.phi;
         uint4* dA = reinterpret_cast<uint4*>(tA_hi);
-        for (size_t i = tid; i < 2 * ta / 16; i += kTile) dA[i] = __ldg(gA + i);
+        for (size_t i = tid; i < 2 * ta / 16; i += kThreads) dA[i] = __ldg(gA + i);
         if constexpr (NBR > 16) {
             const uint4* gB = P.phi + 2 * ta / 16;
             const size_t nb1 = tb / 16;
             uint4* dB = reinterpret_cast<uint4*>(tB_hi);
-            for (size_t i = tid; i < nb1; i += kTile) {
+            for (size_t i = tid; i < nb1; i += kThreads) {
                 dB[i] = __ldg(gB + i);
                 dB[nb1 + i] = __ldg(gB + ta / 16 + i);
             }
@@ -285,15 +272,15 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
     bool ok = true;
 
     const uint64_t keep = l2_policy_evict_last(), last = l2_policy_evict_first();
-    const uint32_t* mrow = P.mask + (p0 >> 5) + (tid >> 5);
+    const uint32_t* mrow = P.mask + (p0 >> 5) + (px >> 5);
 
-    // ---- Y stream: passes over date blocks [b0, b1), read 8 dates at a time in order ----------
-    // TMA loader: block q of the kernel's sequence sits in stage q % S; thread 0
-    // keeps S blocks in flight, refilling a stage once all 128 threads have
-    // arrived on its empty barrier.  Plain loader: per-thread loads two groups
-    // ahead plus L2 prefetch.
+    // ---- Y stream: passes over date blocks [b0, b1) -------------------------------------------
+    // Block q of the kernel's sequence sits in stage q % S; thread 0 keeps S
+    // blocks in flight and refills a stage once its empty barrier has seen 256
+    // arrivals (each thread's, or 2 from each reader when one thread of the
+    // pair reads the whole block).
     uint32_t q_next = 0, s_q0 = 0;
-    int s_b0 = 0, s_b1 = 0;
+    int s_b0 = 0, s_b1 = 0, s_tlim = 0;
     uint64_t s_pol = keep;
     auto issue = [&](uint32_t q, int bd) {  // thread 0
         const int st = (int)(q % (uint32_t)S);
@@ -301,95 +288,48 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
         ptx::mbar_arrive_expect_tx(full + st, kStageBytes);
         tma_load_2d_hint(sY + (size_t)st * kStageBytes, &tmap, full + st, (int)p0, bd * kBlk, s_pol);
     };
-    // plain loader state
-    const int lane = tid & 31;
-    const int64_t pf_px = p0 + (tid & ~31) + 8 * (lane >> 3);
-    const T* pf_col = static_cast<const T*>(P.Y) + (pf_px < P.m ? pf_px : 0);
-    const T* ycol = static_cast<const T*>(P.Y) + (active ? p : 0);
-    int s_tlim = 0, s_pf_from = 0;
-    bool s_pf_keep = true;
-    float ya1[8], ya2[8];
-    uint32_t va1 = 0u, va2 = 0u;
-    auto load8 = [&](int t0, float (&y)[8]) -> uint32_t {
-        uint32_t vb = 0u;
-        const T* a = ycol + (int64_t)t0 * P.m;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            const int t = t0 + e;
-            bool v = false;
-            y[e] = 0.f;
-            if (active && t < s_tlim) {
-                y[e] = YLoad<T>::get(a, s_pol, v);
-                if constexpr (kMask) v = v && ((__ldg(mrow + (size_t)t * P.mask_words) >> (tid & 31)) & 1u);
-            }
-            a += P.m;
-            vb |= (v ? 1u : 0u) << e;
-        }
-        const int tp = t0 + kPrefetch + (lane & 7);
-        if (pf_px < P.m && tp >= s_pf_from && tp < s_tlim) {
-            const T* q = pf_col + (int64_t)tp * P.m;
-            if (s_pf_keep)
-                prefetch_l2_keep(q);
-            else
-                prefetch_l2(q);
-        }
-        return vb;
-    };
-    auto open = [&](int b0, int b1, int tlim, uint64_t pol, int pf_from, bool pf_keep) {
+    auto open = [&](int b0, int b1, int tlim, uint64_t pol) {
         s_b0 = b0;
         s_b1 = b1;
         s_q0 = q_next;
         q_next += (uint32_t)(b1 - b0);
         s_pol = pol;
         s_tlim = tlim;
-        if constexpr (kTMA) {
-            if (tid == 0)
-                for (int j = 0; j < S && b0 + j < b1; ++j) issue(s_q0 + (uint32_t)j, b0 + j);
-        } else {
-            s_pf_from = pf_from;
-            s_pf_keep = pf_keep;
-            va1 = load8(b0 * kBlk, ya1);
-            va2 = load8(b0 * kBlk + 8, ya2);
-        }
+        if (tid == 0)
+            for (int j = 0; j < S && b0 + j < b1; ++j) issue(s_q0 + (uint32_t)j, b0 + j);
     };
-    // dates [t0, t0 + 8) of this pixel: values (0 where invalid) and valid bits
-    // (missing, masked, t >= tlim and pixels beyond m are invalid)
-    auto next8 = [&](int t0, float (&y)[8]) -> uint32_t {
-        if constexpr (kTMA) {
-            const int bd = t0 / kBlk, half = (t0 / 8) & 1;
-            const uint32_t q = s_q0 + (uint32_t)(bd - s_b0);
-            const int st = (int)(q % (uint32_t)S);
-            if (half == 0) ok &= ptx::mbar_wait_bounded(full + st, (q / S) & 1u, kWaitNs);
-            const unsigned char* sb = sY + (size_t)st * kStageBytes;
-            uint32_t vb = 0u;
+    // the stage of date block bd, waited for
+    auto block_wait = [&](int bd) -> const unsigned char* {
+        const uint32_t q = s_q0 + (uint32_t)(bd - s_b0);
+        const int st = (int)(q % (uint32_t)S);
+        ok &= ptx::mbar_wait_bounded(full + st, (q / S) & 1u, kWaitNs);
+        return sY + (size_t)st * kStageBytes;
+    };
+    // done with block bd: `count` arrivals, then thread 0 refills the stage
+    auto block_release = [&](int bd, uint32_t count) {
+        const uint32_t q = s_q0 + (uint32_t)(bd - s_b0);
+        const int st = (int)(q % (uint32_t)S);
+        mbar_arrive_cnt(empty + st, count);
+        if (tid == 0 && bd + S < s_b1) issue(q + (uint32_t)S, bd + S);
+    };
+    // dates [t0, t0 + 8) of this pixel from a waited stage: values (0 where
+    // invalid) and valid bits (missing, masked, t >= tlim, pixel beyond m)
+    auto read8 = [&](const unsigned char* sb, int t0, float (&y)[8]) -> uint32_t {
+        const int r0 = t0 & (kBlk - 1);
+        uint32_t vb = 0u;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int t = t0 + e;
-                bool v;
-                const float x = YSmem<T>::get(sb, (half * 8 + e) * kTile + tid, v);
-                v = v && active && t < s_tlim;
-                if constexpr (kMask) {
-                    if (v) v = (__ldg(mrow + (size_t)t * P.mask_words) >> (tid & 31)) & 1u;
-                }
-                y[e] = v ? x : 0.f;
-                vb |= (v ? 1u : 0u) << e;
+        for (int e = 0; e < 8; ++e) {
+            const int t = t0 + e;
+            bool v;
+            const float x = YSmem<T>::get(sb, (r0 + e) * kTile + px, v);
+            v = v && active && t < s_tlim;
+            if constexpr (kMask) {
+                if (v) v = (__ldg(mrow + (size_t)t * P.mask_words) >> (px & 31)) & 1u;
             }
-            if (half == 1) {
-                mbar_arrive(empty + st);
-                if (tid == 0 && bd + S < s_b1) issue(q + (uint32_t)S, bd + S);
-            }
-            return vb;
-        } else {
-            const uint32_t v = va1;
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                y[e] = ((v >> e) & 1u) ? ya1[e] : 0.f;  // the slots past tlim keep stale values
-                ya1[e] = ya2[e];
-            }
-            va1 = va2;
-            va2 = t0 + 16 < s_tlim ? load8(t0 + 16, ya2) : 0u;
-            return v;
+            y[e] = v ? x : 0.f;
+            vb |= (v ? 1u : 0u) << e;
         }
+        return vb;
     };
 
     uint32_t done_uses = 0, buf_uses[2] = {0u, 0u};
@@ -402,56 +342,68 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
     auto acquire = [&](int b) {
         if (buf_uses[b]) ok &= ptx::mbar_wait_bounded(bar_buf + b, (buf_uses[b] - 1u) & 1u, kWaitNs);
     };
+    // the pair partner's value of x (both threads call it)
+    auto pair_exchange = [&](float x) -> float {
+        sX[tid] = x;
+        __syncthreads();
+        const float o = sX[tid ^ kTile];
+        __syncthreads();
+        return o;
+    };
     const int nbh = (n_hist + kBlk - 1) / kBlk;  // history blocks
 
     // ---- normal equations (Eq. 6): masked basis sums and X'My over the history --------------
-    // A rows per 16-date chunk: the 0/1 mask, and y*s_y split into fp16 hi + lo
-    // (int16: 256*(y >> 8) and y & 255, both exact; float: a per-pixel power of
-    // two s_y from the first eight dates holding a valid value, redone from the
-    // history maximum if a value of the tile leaves the range where the split
-    // keeps 22 bits).
+    // A rows per 16-date chunk (this thread: group `half`): the 0/1 mask, and
+    // y*s_y split into fp16 hi + lo (int16: 256*(y >> 8) and y & 255, both
+    // exact; float: a per-pixel power of two s_y from the first group of
+    // eight dates holding a valid value (both threads of the pair look at
+    // both groups until then), redone from the history maximum if a value of
+    // the tile leaves the range where the split keeps 22 bits).
     float ymax = 0.f, s_y = 1.f;
     bool s_set = kInt;
     for (int attempt = 0; attempt < 2; ++attempt) {
-        open(0, nbh, n_hist, keep, 0, true);
-        ymax = 0.f;
+        open(0, nbh, n_hist, keep);
+        float ym = 0.f;
         for (int c = 0; c < nbh; ++c) {
             const int buf = c & 1;
             unsigned char* pl = sA + (size_t)buf * kBufBytes;
             acquire(buf);
-#pragma unroll 1
-            for (int g = 0; g < 2; ++g) {
-                const int t0 = c * kBlk + g * 8;
-                float yc[8];
-                const uint32_t vc = next8(t0, yc);
-                if (!s_set) {  // float: the first group with a valid value sets s_y (earlier rows are 0)
+            const unsigned char* sb = block_wait(c);
+            float yc[8];
+            if (!s_set) {  // float: the first group with a valid value sets s_y (earlier rows are 0)
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    float yg[8];
+                    read8(sb, c * kBlk + g * 8, yg);
                     float gm = 0.f;
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) gm = fmaxf(gm, fabsf(yc[e]));
-                    if (gm > 0.f) {
+                    for (int e = 0; e < 8; ++e) gm = fmaxf(gm, fabsf(yg[e]));
+                    if (!s_set && gm > 0.f) {
                         s_y = pow2_scale(gm, 4);
                         s_set = true;
                     }
                 }
-                float mk[8], a1[8], a2[8];
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const bool v = (vc >> e) & 1u;
-                    mk[e] = v ? 1.f : 0.f;
-                    const float y = yc[e];
-                    ymax = fmaxf(ymax, fabsf(y));
-                    if constexpr (kInt) {
-                        const int yi = (int)y;
-                        a1[e] = (float)((yi >> 8) * 256);
-                        a2[e] = (float)(yi & 255);
-                    } else {
-                        split_hi_lo(y * s_y, a1[e], a2[e]);
-                    }
-                }
-                st_a(pl, tid, g, mk);
-                st_a(pl + kPlane, tid, g, a1);
-                st_a(pl + 2 * kPlane, tid, g, a2);
             }
+            const uint32_t vc = read8(sb, c * kBlk + half * 8, yc);
+            block_release(c, 1);
+            float mk[8], a1[8], a2[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const bool v = (vc >> e) & 1u;
+                mk[e] = v ? 1.f : 0.f;
+                const float y = yc[e];
+                ym = fmaxf(ym, fabsf(y));
+                if constexpr (kInt) {
+                    const int yi = (int)y;
+                    a1[e] = (float)((yi >> 8) * 256);
+                    a2[e] = (float)(yi & 255);
+                } else {
+                    split_hi_lo(y * s_y, a1[e], a2[e]);
+                }
+            }
+            st_a(pl, px, half, mk);
+            st_a(pl + kPlane, px, half, a1);
+            st_a(pl + 2 * kPlane, px, half, a2);
             ptx::fence_async_smem();
             ptx::tc_fence_before();
             __syncthreads();
@@ -475,6 +427,7 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
             ++buf_uses[buf];
         }
         wait_done();
+        ymax = fmaxf(ym, pair_exchange(ym));
         if (kInt) break;
         const float qy = ymax * s_y;
         const bool redo = ymax > 0.f && !(qy < 32768.f && qy >= 4.f);
@@ -483,7 +436,7 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
         s_set = true;
     }
 
-    // ---- solve ---------------------------------------------------------------------------
+    // ---- solve (both threads of the pair, identically) -------------------------------------------
     float a[NBR], bb[K];
     {
         float v32[32], v16[16];
@@ -521,26 +474,20 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
             split_hi_lo(cs, h[i], l[i]);
             z[i] = 0.f;
         }
-        st_a(hi_plane, tid, 0, h);
-        st_a(hi_plane, tid, 1, z);
-        st_a(lo_plane, tid, 0, l);
-        st_a(lo_plane, tid, 1, z);
+        st_a(hi_plane, px, 0, h);
+        st_a(hi_plane, px, 1, z);
+        st_a(lo_plane, px, 0, l);
+        st_a(lo_plane, px, 1, z);
     };
-    write_coef(beta, sC, sC + kCoefPlane);
+    if (half == 0) write_coef(beta, sC, sC + kCoefPlane);
     const float inv_b = 1.f / s_b;
 
-    // Bandwidth h (Eq. 3, missing-data reading) and the position n - h + 1 of
-    // the earliest history observation a monitoring window reaches back to.
-    int h = (int)floor(P.h_frac * (double)n_i);
-    if (h < 1) h = 1;
-    if (h > n_i) h = n_i;
-    const int target = n_i - h + 1;
-    int cpos = 0, dfirst = N;
-
     // ---- one refinement step: r0 = y - X beta0 on the history, c = X'M r0 ------------------
-    // X beta0 comes from the tensor cores, kPiece dates per TMEM piece.
+    // X beta0 comes from the tensor cores, kPiece dates per TMEM piece; each
+    // thread of the pair takes its group of every chunk and records the
+    // group's valid bits.
     float ss = 0.f;
-    open(0, nbh, n_hist, keep, 1 << 30, true);
+    open(0, nbh, n_hist, keep);
     for (int d0 = 0; d0 < nbh * kBlk; d0 += kPiece) {
         const int w = nbh * kBlk - d0 < kPiece ? nbh * kBlk - d0 : kPiece;
         ptx::fence_async_smem();
@@ -553,18 +500,21 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
         }
         wait_done();
         uint32_t rq[8];
-        ptx::tmem_ld8_issue(tmem + lane_base + kColY, rq);
+        ptx::tmem_ld8_issue(tmem + lane_base + kColY + (uint32_t)(half * 8), rq);
 #pragma unroll 1
-        for (int t0 = d0; t0 < d0 + w; t0 += 8) {
-            const int c = t0 / kBlk, g = (t0 / 8) & 1, buf = c & 1;
+        for (int c = d0 / kBlk; c < (d0 + w) / kBlk; ++c) {
+            const int buf = c & 1;
+            const int t0 = c * kBlk + half * 8;
             unsigned char* pl = sA + (size_t)buf * kBufBytes;
-            if (g == 0) acquire(buf);
+            acquire(buf);
             float yc[8], yh[8];
-            const uint32_t vc = next8(t0, yc);
+            const unsigned char* sb = block_wait(c);
+            const uint32_t vc = read8(sb, t0, yc);
+            block_release(c, 1);
             ptx::tmem_wait_ld8(rq);
 #pragma unroll
             for (int e = 0; e < 8; ++e) yh[e] = __uint_as_float(rq[e]);
-            if (t0 + 8 < d0 + w) ptx::tmem_ld8_issue(tmem + lane_base + kColY + (uint32_t)(t0 + 8 - d0), rq);
+            if (t0 + kBlk < d0 + w) ptx::tmem_ld8_issue(tmem + lane_base + kColY + (uint32_t)(t0 + kBlk - d0), rq);
             float rh[8], rl[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
@@ -572,30 +522,47 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
                 const float r0 = v ? (yc[e] - yh[e] * inv_b) : 0.f;
                 ss = fmaf(r0, r0, ss);
                 split_hi_lo(r0 * s_r, rh[e], rl[e]);
-                cpos += v ? 1 : 0;
-                dfirst = (v && cpos == target) ? t0 + e : dfirst;
             }
-            st_a(pl, tid, g, rh);
-            st_a(pl + kPlane, tid, g, rl);
-            if (g == 1) {
-                ptx::fence_async_smem();
-                ptx::tc_fence_before();
-                __syncthreads();
-                if (tid == 0) {
-                    ptx::tc_fence_after();
-                    const int dd = c * kBlk;
-                    const bool first = c == 0;
-                    mma_kb(tmem + kColC, pl, 0, tA_hi, dd, !first);
-                    mma_kb(tmem + kColC, pl, 0, tA_lo, dd, true);
-                    mma_kb(tmem + kColC, pl + kPlane, 0, tA_hi, dd, true);
-                    ptx::mma_commit(bar_buf + buf);
-                    if (c == nbh - 1) ptx::mma_commit(bar_done);
-                }
-                ++buf_uses[buf];
+            sVb[(c * 2 + half) * kTile + px] = (unsigned char)vc;
+            st_a(pl, px, half, rh);
+            st_a(pl + kPlane, px, half, rl);
+            ptx::fence_async_smem();
+            ptx::tc_fence_before();
+            __syncthreads();
+            if (tid == 0) {
+                ptx::tc_fence_after();
+                const int dd = c * kBlk;
+                const bool first = c == 0;
+                mma_kb(tmem + kColC, pl, 0, tA_hi, dd, !first);
+                mma_kb(tmem + kColC, pl, 0, tA_lo, dd, true);
+                mma_kb(tmem + kColC, pl + kPlane, 0, tA_hi, dd, true);
+                ptx::mma_commit(bar_buf + buf);
+                if (c == nbh - 1) ptx::mma_commit(bar_done);
             }
+            ++buf_uses[buf];
         }
     }
     wait_done();
+    ss += pair_exchange(ss);
+    // Bandwidth h (Eq. 3, missing-data reading) and the date of the earliest
+    // history observation a monitoring window reaches back to: the h-th valid
+    // one from the end of the history.
+    int h = (int)floor(P.h_frac * (double)n_i);
+    if (h < 1) h = 1;
+    if (h > n_i) h = n_i;
+    int dfirst = N;
+    {
+        int cnt = 0;
+        for (int q = 2 * nbh - 1; q >= 0 && cnt < h; --q) {
+            uint32_t byte = sVb[q * kTile + px];
+            const int pc = __popc(byte);
+            if (cnt + pc >= h) {
+                for (int k = cnt; k < h - 1; ++k) byte &= ~(0x80000000u >> __clz(byte));  // drop the top set bits
+                dfirst = q * 8 + (31 - __clz(byte));
+            }
+            cnt += pc;
+        }
+    }
     float sigma, scale;
     int jlim;
     float dl[K];
@@ -616,17 +583,18 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
         scale = sigma * sqrtf((float)n_i);
         jlim = (int)floor(kEuler * (double)n_i);
     }
-    write_coef(dl, sC + 2 * kCoefPlane, sC + 3 * kCoefPlane);
+    __syncthreads();  // valid bytes read by both threads before the delta planes overwrite them
+    if (half == 0) write_coef(dl, sC + 2 * kCoefPlane, sC + 3 * kCoefPlane);
     const bool degenerate = !(sigma > kDegenerateRatio * ymax) || ymax == 0.f;
     // The MOSUM pass starts at the earliest such date over the tile's pixels
     // that get a break test (prefix sums from there on differ from those
     // from date 0 by a constant, which the window differences cancel).
-    if (active && n_i > K && nonsingular && !degenerate) atomicMin(s_dstart, dfirst);
+    if (half == 0 && active && n_i > K && nonsingular && !degenerate) atomicMin(s_dstart, dfirst);
     __syncthreads();
     int d_start = *s_dstart;
     d_start = (d_start < n_hist ? d_start : n_hist) / kBlk * kBlk;
 
-    // ---- MOSUM from d_start, 8 dates at a time -------------------------------------------------
+    // ---- MOSUM from d_start, 8 dates at a time (first thread of each pair) -----------------------
     // yhat = X beta0 + X delta per kPiece-date TMEM piece (the fp16 split error
     // of beta0 lies in the span of X and cancels against the refinement).  Per
     // 8-date group: residuals and validity independently; compensated prefix
@@ -643,7 +611,7 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
     const float inv_scale = 1.f / scale, lam2 = P.lambda * P.lambda;
     const float lg_n = log2f((float)n_i);
     const int nball = (N + kBlk - 1) / kBlk;
-    open(d_start / kBlk, nball, N, last, n_hist, false);
+    open(d_start / kBlk, nball, N, last);
     for (int d0 = d_start; d0 < P.npad; d0 += kPiece) {
         const int w = P.npad - d0 < kPiece ? P.npad - d0 : kPiece;
         ptx::fence_async_smem();
@@ -656,13 +624,18 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
             ptx::mma_commit(bar_done);
         }
         wait_done();
+        if (half == 1) continue;  // (warp-uniform) the second thread of each pair idles here
         const int dend = d0 + w < nball * kBlk ? d0 + w : nball * kBlk;  // whole Y blocks
         uint32_t rq[8];
         if (d0 < dend) ptx::tmem_ld8_issue(tmem + lane_base + kColY, rq);
+        const unsigned char* sb = nullptr;
 #pragma unroll 1
         for (int c0 = d0; c0 < dend; c0 += 8) {
             float yc[8], yh[8];
-            const uint32_t vb = next8(c0, yc);
+            const int bd = c0 / kBlk;
+            if ((c0 & 8) == 0) sb = block_wait(bd);
+            const uint32_t vb = read8(sb, c0, yc);
+            if (c0 & 8) block_release(bd, 2);
             ptx::tmem_wait_ld8(rq);
 #pragma unroll
             for (int e = 0; e < 8; ++e) yh[e] = __uint_as_float(rq[e]);
@@ -698,7 +671,7 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
                 const int v = (vb >> e) & 1u;
-                if (v) ring[slot * kTile + tid] = Sv[e];
+                if (v) ring[slot * kTile + px] = Sv[e];
                 sl[e] = slot;
                 slot += v;
                 slot = slot == R ? 0 : slot;
@@ -711,7 +684,7 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
                 for (int e = 0; e < 8; ++e) {
                     int ls = sl[e] - h;
                     ls += ls < 0 ? R : 0;
-                    const float W = Sv[e] - ring[ls * kTile + tid];
+                    const float W = Sv[e] - ring[ls * kTile + px];
                     const float mo = W * inv_scale;
                     const int J = n_i + jq + 1;
                     const float b2 = J > jlim ? lam2 * kLn2f * (log2_fast((float)J) - lg_n) : lam2;
@@ -734,7 +707,8 @@ __global__ void __launch_bounds__(kTile, 1) mma_kernel(const __grid_constant__ C
     ptx::tc_fence_before();
     __syncthreads();
     if (warp == 0) ptx::tmem_dealloc(tmem, kTmemCols);
-    if (!active) return;
+    if (!__syncthreads_and(ok ? 1 : 0)) ok = false;
+    if (!active || half == 1) return;
     if (!ok) {
         P.status[p] = BFM_PX_TIMEOUT;
         atomicOr(&g_bfm_mma_err, 2u);
@@ -820,9 +794,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn_mma() {
     return fn;
 }
 
-template <int KH, typename T, bool kTMA>
+template <int KH, typename T>
 bfm_status launch_t(const CUtensorMap& tm, const MmaParams& P, size_t smem, cudaStream_t stream) {
-    auto kern = P.mask ? mma_kernel<KH, T, true, kTMA> : mma_kernel<KH, T, false, kTMA>;
+    auto kern = P.mask ? mma_kernel<KH, T, true> : mma_kernel<KH, T, false>;
     static thread_local int configured[2] = {-1, -1};
     int dev = 0;
     cudaGetDevice(&dev);
@@ -832,21 +806,24 @@ bfm_status launch_t(const CUtensorMap& tm, const MmaParams& P, size_t smem, cuda
         configured[P.mask ? 1 : 0] = dev;
     }
     const unsigned grid = (unsigned)((P.m + kTile - 1) / kTile);
-    kern<<<grid, kTile, smem, stream>>>(tm, P);
+    kern<<<grid, kThreads, smem, stream>>>(tm, P);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "mma kernel launch");
     return BFM_OK;
 }
 
-template <int KH, typename T>
-bfm_status launch_k(const CUtensorMap& tm, bool tma, const MmaParams& P, size_t smem, cudaStream_t stream) {
-    return tma ? launch_t<KH, T, true>(tm, P, smem, stream) : launch_t<KH, T, false>(tm, P, smem, stream);
-}
-
 }  // namespace
 
-bool mma_supported(const bfm_design_s* d, int dtype, int n_hist, double h_frac, size_t* smem_out) {
+// Y must be describable by a tensor map with boxes of 128 pixels x 16 dates.
+bool mma_layout_ok(const void* Y, int dtype, int64_t m) {
+    const int elt = dtype == BFM_F32 ? 4 : 2;
+    return m == 0 || (((uintptr_t)Y % 16 == 0) && ((m * elt) % 16 == 0) && m >= kTile);
+}
+
+bool mma_supported(const bfm_design_s* d, int dtype, int n_hist, double h_frac, const void* Y, int64_t m,
+                   size_t* smem_out) {
     if ((dtype != BFM_I16 && dtype != BFM_F32) || !d->d_phi_tc || d->N > kTcMaxDates) return false;
+    if (!mma_layout_ok(Y, dtype, m)) return false;
     const MmaLayout L = mma_layout(d->npad_tc, (n_hist + 31) / 32 * 32, d->k, ring_len(n_hist, h_frac),
                                    dtype == BFM_F32 ? 4 : 2, true);
     if (smem_out) *smem_out = L.smem;
@@ -878,31 +855,37 @@ bfm_status launch_mma(const bfm_design_s* d, int dtype, const void* Y, const uin
     P.sigma = sigma;
     P.beta = beta;
     P.status = status;
-    // TMA loader when the layout allows boxes of 128 pixels x 16 dates
     CUtensorMap tm;
     std::memset(&tm, 0, sizeof tm);
-    bool tma = ((uintptr_t)Y % 16 == 0) && ((m * elt) % 16 == 0) && m >= kTile;
-    if (tma) {
-        auto enc = encode_fn_mma();
+    auto enc = encode_fn_mma();
+    if (!mma_layout_ok(Y, dtype, m) || !enc) {
+        set_error("tensor-core form: Y needs a 16-byte aligned base, m >= 128 and rows of a multiple of 16 bytes");
+        return BFM_EUNSUPPORTED;
+    }
+    {
         cuuint64_t gdim[2] = {(cuuint64_t)m, (cuuint64_t)d->N};
         cuuint64_t gstride[1] = {(cuuint64_t)m * elt};
         cuuint32_t box[2] = {(cuuint32_t)kTile, (cuuint32_t)kBlk};
         cuuint32_t es[2] = {1u, 1u};
-        tma = enc && enc(&tm, elt == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 2,
-                         const_cast<void*>(Y), gdim, gstride, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+        const CUresult r = enc(&tm, elt == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 2,
+                               const_cast<void*>(Y), gdim, gstride, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            set_error("tensor-core form: cuTensorMapEncodeTiled failed for Y");
+            return BFM_EUNSUPPORTED;
+        }
     }
-    const MmaLayout L = mma_layout(P.npad, P.nhpad, d->k, P.ring, elt, tma);
+    const MmaLayout L = mma_layout(P.npad, P.nhpad, d->k, P.ring, elt, true);
     P.stages = L.stages;
     P.region_bytes = L.region_bytes;
     // At least 80 KB, so that at most two CTAs (2 x 256 TMEM columns) share an SM.
     size_t smem = L.smem < 80 * 1024 ? 80 * 1024 : L.smem;
     const bool i16 = dtype == BFM_I16;
     switch (d->k) {
-        case 1: return i16 ? launch_k<1, int16_t>(tm, tma, P, smem, stream) : launch_k<1, float>(tm, tma, P, smem, stream);
-        case 2: return i16 ? launch_k<2, int16_t>(tm, tma, P, smem, stream) : launch_k<2, float>(tm, tma, P, smem, stream);
-        default: return i16 ? launch_k<3, int16_t>(tm, tma, P, smem, stream) : launch_k<3, float>(tm, tma, P, smem, stream);
+        case 1: return i16 ? launch_t<1, int16_t>(tm, P, smem, stream) : launch_t<1, float>(tm, P, smem, stream);
+        case 2: return i16 ? launch_t<2, int16_t>(tm, P, smem, stream) : launch_t<2, float>(tm, P, smem, stream);
+        default: return i16 ? launch_t<3, int16_t>(tm, P, smem, stream) : launch_t<3, float>(tm, P, smem, stream);
     }
 }
 

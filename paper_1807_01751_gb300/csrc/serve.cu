@@ -218,7 +218,7 @@ void start(bfm_server_s* s, Req* q, int slot) {
     } else if (r.m > 0) {
         int algo = r.algo;
         if (algo == BFM_ALGO_AUTO || algo == BFM_ALGO_MMA) {
-            const bool ok = mma_supported(r.design, r.dtype, r.n_hist, r.h_frac, nullptr);
+            const bool ok = mma_supported(r.design, r.dtype, r.n_hist, r.h_frac, Y, r.m, nullptr);
             algo = ok ? BFM_ALGO_MMA : BFM_ALGO_SIMT;
         }
         bs = algo == BFM_ALGO_MMA

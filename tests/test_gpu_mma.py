@@ -74,12 +74,27 @@ def test_c1_f32(bfm):
 
 
 @pytest.mark.parametrize("dtype", ["i16", "f32"])
-@pytest.mark.parametrize("m", [1, 100, 129, 1000, 4093, 4104])
+@pytest.mark.parametrize("m", [128, 136, 1000, 4104, 4232])
 def test_ragged(bfm, m, dtype):
-    """m < 128 (one partial tile), m % 128 != 0 (ragged last tile) and odd m."""
+    """One full tile, and ragged last tiles of 8, 104 and 8 live pixels (the
+    TMA box reads zeros past m; those pixels are not written)."""
     w = synth.workload("c3" if dtype == "i16" else "c1", m=m)
     g = _run(bfm, w["dates"], w["Y"], k=3, n_hist=w["n_hist"], h_frac=w["h_frac"], lam=w["lam"])
     _check(w["dates"], w["Y"], g, k=3, n_hist=w["n_hist"], h_frac=w["h_frac"], lam=w["lam"])
+
+
+@pytest.mark.parametrize("dtype", ["i16", "f32"])
+@pytest.mark.parametrize("m", [1, 100, 129, 4093])
+def test_untileable_layout_is_refused(bfm, m, dtype):
+    """m < 128 or rows that are not a multiple of 16 bytes: no tensor map for
+    Y, so algo = MMA is BFM_EUNSUPPORTED and AUTO takes the CUDA-core form."""
+    w = synth.workload("c3" if dtype == "i16" else "c1", m=m)
+    kw = dict(k=3, n_hist=w["n_hist"], h_frac=w["h_frac"], lam=w["lam"])
+    with pytest.raises(bfm.BfmError) as ei:
+        _run(bfm, w["dates"], w["Y"], **kw)
+    assert ei.value.code == 6
+    g = _run(bfm, w["dates"], w["Y"], algo=0, **kw)
+    _check(w["dates"], w["Y"], g, tol=1e-5, **kw)
 
 
 def test_f32_value_ranges(bfm):

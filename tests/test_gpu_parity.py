@@ -59,11 +59,12 @@ def test_c1_full_tma(bfm, algo):
     assert (ref["break_idx"] >= 0).sum() > 500
 
 
-@ALGOS
+@pytest.mark.parametrize("algo", [0, 1], ids=["auto", "simt"])
 @pytest.mark.parametrize("m", [1, 31, 33, 129, 4093])
 def test_c1_ragged_plain_loader(bfm, m, algo):
-    """m not a multiple of 4 (or < 32) takes the plain-load tile loader; the
-    last tile is ragged."""
+    """m not a multiple of 4 (or < 32) takes the plain-load tile loader of the
+    CUDA-core form (AUTO picks it: the tensor-core form needs a TMA-describable
+    Y); the last tile is ragged."""
     w = synth.workload("c1", m=m)
     gpu = _run(bfm, w, w["Y"], algo=algo)
     _check(w, w["Y"], gpu)
@@ -115,7 +116,7 @@ def test_edge_statuses(bfm, algo):
     """Pixels crafted for every status, placed on tile boundaries (lanes 0,
     31, 32, 63): all missing, too few history obs, no monitoring data,
     noise-free (degenerate), collinear history (singular)."""
-    w = synth.workload("c1", m=96)
+    w = synth.workload("c1", m=128 if algo == 2 else 96)
     Y = w["Y"].copy()
     N, n = w["N"], w["n_hist"]
     Y[:, 0] = np.nan
