@@ -65,7 +65,7 @@ enum {
 
 /* Algorithm variants for bfm_monitor_ex.  BFM_ALGO_AUTO takes the
  * tensor-core form where it applies (N <= 448 and a MOSUM ring of
- * floor(h_frac * n_hist) + 9 prefix sums per pixel that fits shared memory
+ * floor(h_frac * n_hist) + 17 prefix sums per pixel that fits shared memory
  * next to the basis tables: up to about 300 at N = 448), else the CUDA-core
  * form. */
 typedef enum {

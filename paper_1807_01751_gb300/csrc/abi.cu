@@ -336,7 +336,7 @@ bfm_status bfm_monitor_ex(bfm_design_t d, const void* Y, int dtype, const uint32
     }
     const bool mma_ok = mma_supported(d, dtype, n_hist, h_frac, Y, m, nullptr);
     if (algo == BFM_ALGO_MMA && !mma_ok) {
-        set_error("bfm_monitor: the tensor-core form needs N <= 448, a MOSUM ring (bandwidth + 9 prefix sums per pixel) that fits shared memory, and Y with a 16-byte aligned base, m >= 128 and rows of a multiple of 16 bytes");
+        set_error("bfm_monitor: the tensor-core form needs N <= 448, a MOSUM ring (bandwidth + 17 prefix sums per pixel) that fits shared memory, and Y with a 16-byte aligned base, m >= 128 and rows of a multiple of 16 bytes");
         return BFM_EUNSUPPORTED;
     }
     if (algo == BFM_ALGO_MMA || (algo == BFM_ALGO_AUTO && mma_ok))

@@ -227,7 +227,9 @@ __global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant_
     uint64_t* bar_done = bars + 2;
     uint64_t* full = bars + 3;                 // [S] Y block landed
     uint64_t* empty = bars + 3 + kMaxStages;   // [S] Y block released (256 arrivals)
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 3 + 2 * kMaxStages);
+    uint64_t* rdy = bars + 3 + 2 * kMaxStages;  // [2] MOSUM group published by the first threads
+    uint64_t* cons = rdy + 2;                    // [2] MOSUM group consumed by the second threads
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(cons + 2);
     int* s_dstart = reinterpret_cast<int*>(tslot + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -243,6 +245,10 @@ __global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant_
         for (int i = 0; i < S; ++i) {
             ptx::mbar_init(full + i, 1);
             ptx::mbar_init(empty + i, kThreads);
+        }
+        for (int i = 0; i < 2; ++i) {
+            ptx::mbar_init(rdy + i, kTile);
+            ptx::mbar_init(cons + i, kTile);
         }
         ptx::fence_mbar_init();
         *s_dstart = N;
@@ -275,14 +281,15 @@ __global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant_
     const uint32_t* mrow = P.mask + (p0 >> 5) + (px >> 5);
 
     // ---- Y stream: passes over date blocks [b0, b1) -------------------------------------------
-    // Block q of the kernel's sequence sits in stage q % S; thread 0 keeps S
-    // blocks in flight and refills a stage once its empty barrier has seen 256
-    // arrivals (each thread's, or 2 from each reader when one thread of the
-    // pair reads the whole block).
+    // Block q of the kernel's sequence sits in stage q % S; the producer
+    // thread keeps S blocks in flight and refills a stage once its empty
+    // barrier has seen 256 arrivals (the producer's 256 after a chunk barrier
+    // in the history passes, 2 from each first thread in the MOSUM pass).
     uint32_t q_next = 0, s_q0 = 0;
     int s_b0 = 0, s_b1 = 0, s_tlim = 0;
+    int producer = 0;  // thread 0 in the history passes, thread 128 in the MOSUM pass
     uint64_t s_pol = keep;
-    auto issue = [&](uint32_t q, int bd) {  // thread 0
+    auto issue = [&](uint32_t q, int bd) {  // the producer thread
         const int st = (int)(q % (uint32_t)S);
         if (q >= (uint32_t)S) ok &= ptx::mbar_wait_bounded(empty + st, ((q / S) - 1u) & 1u, kWaitNs);
         ptx::mbar_arrive_expect_tx(full + st, kStageBytes);
@@ -295,7 +302,7 @@ __global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant_
         q_next += (uint32_t)(b1 - b0);
         s_pol = pol;
         s_tlim = tlim;
-        if (tid == 0)
+        if (tid == producer)
             for (int j = 0; j < S && b0 + j < b1; ++j) issue(s_q0 + (uint32_t)j, b0 + j);
     };
     // the stage of date block bd, waited for
@@ -305,31 +312,46 @@ __global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant_
         ok &= ptx::mbar_wait_bounded(full + st, (q / S) & 1u, kWaitNs);
         return sY + (size_t)st * kStageBytes;
     };
-    // done with block bd: `count` arrivals, then thread 0 refills the stage
+    // done with block bd: `count` arrivals (the producer refills the stage later)
     auto block_release = [&](int bd, uint32_t count) {
         const uint32_t q = s_q0 + (uint32_t)(bd - s_b0);
-        const int st = (int)(q % (uint32_t)S);
-        mbar_arrive_cnt(empty + st, count);
-        if (tid == 0 && bd + S < s_b1) issue(q + (uint32_t)S, bd + S);
+        mbar_arrive_cnt(empty + (int)(q % (uint32_t)S), count);
+    };
+    auto block_refill = [&](int bd) {  // the producer thread
+        const uint32_t q = s_q0 + (uint32_t)(bd - s_b0);
+        if (bd + S < s_b1) issue(q + (uint32_t)S, bd + S);
     };
     // dates [t0, t0 + 8) of this pixel from a waited stage: values (0 where
     // invalid) and valid bits (missing, masked, t >= tlim, pixel beyond m)
     auto read8 = [&](const unsigned char* sb, int t0, float (&y)[8]) -> uint32_t {
         const int r0 = t0 & (kBlk - 1);
+        const int nt = s_tlim - t0;  // dates of the group before tlim
+        const uint32_t lim = !active || nt <= 0 ? 0u : (nt >= 8 ? 0xffu : (1u << nt) - 1u);
         uint32_t vb = 0u;
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            const int t = t0 + e;
             bool v;
-            const float x = YSmem<T>::get(sb, (r0 + e) * kTile + px, v);
-            v = v && active && t < s_tlim;
-            if constexpr (kMask) {
-                if (v) v = (__ldg(mrow + (size_t)t * P.mask_words) >> (px & 31)) & 1u;
-            }
-            y[e] = v ? x : 0.f;
+            y[e] = YSmem<T>::get(sb, (r0 + e) * kTile + px, v);
             vb |= (v ? 1u : 0u) << e;
         }
+        vb &= lim;
+        if constexpr (kMask) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+                if ((vb >> e) & 1u)
+                    vb &= ~((((__ldg(mrow + (size_t)(t0 + e) * P.mask_words) >> (px & 31)) & 1u) ^ 1u) << e);
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) y[e] = ((vb >> e) & 1u) ? y[e] : 0.f;
         return vb;
+    };
+    // history passes: after the chunk's barrier every thread is done with
+    // block c, so thread 0 completes its empty phase at once and refills it
+    auto chunk_release = [&](int bd) {
+        if (tid == producer) {
+            block_release(bd, kThreads);
+            block_refill(bd);
+        }
     };
 
     uint32_t done_uses = 0, buf_uses[2] = {0u, 0u};
@@ -385,7 +407,6 @@ __global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant_
                 }
             }
             const uint32_t vc = read8(sb, c * kBlk + half * 8, yc);
-            block_release(c, 1);
             float mk[8], a1[8], a2[8];
 #pragma unroll
             for (int e = 0; e < 8; ++e) {
@@ -407,6 +428,7 @@ __global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant_
             ptx::fence_async_smem();
             ptx::tc_fence_before();
             __syncthreads();
+            chunk_release(c);
             if (tid == 0) {
                 ptx::tc_fence_after();
                 const int d0 = c * kBlk;
@@ -510,7 +532,6 @@ __global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant_
             float yc[8], yh[8];
             const unsigned char* sb = block_wait(c);
             const uint32_t vc = read8(sb, t0, yc);
-            block_release(c, 1);
             ptx::tmem_wait_ld8(rq);
 #pragma unroll
             for (int e = 0; e < 8; ++e) yh[e] = __uint_as_float(rq[e]);
@@ -529,6 +550,7 @@ __global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant_
             ptx::fence_async_smem();
             ptx::tc_fence_before();
             __syncthreads();
+            chunk_release(c);
             if (tid == 0) {
                 ptx::tc_fence_after();
                 const int dd = c * kBlk;
@@ -594,16 +616,21 @@ __global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant_
     int d_start = *s_dstart;
     d_start = (d_start < n_hist ? d_start : n_hist) / kBlk * kBlk;
 
-    // ---- MOSUM from d_start, 8 dates at a time (first thread of each pair) -----------------------
-    // yhat = X beta0 + X delta per kPiece-date TMEM piece (the fp16 split error
-    // of beta0 lies in the span of X and cancels against the refinement).  Per
-    // 8-date group: residuals and validity independently; compensated prefix
-    // sums S over valid positions into a ring of R >= h + 9 slots; then the
-    // windows W_J = S_J - S_{J-h} (Eq. 3) of the group's monitoring positions
-    // J = n + 1, n + 2, ..., scaled to MO_J = W_J / (sigma-hat sqrt(n)) and
-    // tested as MO_J^2 > lambda^2 log+(J/n) (Eq. 4, squared).  Branch-free:
-    // invalid dates add 0 and their (in-range) lag reads are masked.
+    // ---- MOSUM from d_start, 8 dates at a time, as a two-stage pipeline per pixel ----------------
+    // First thread of the pair: yhat = X beta0 + X delta per kPiece-date TMEM
+    // piece (the fp16 split error of beta0 lies in the span of X and cancels
+    // against the refinement); per 8-date group the residuals, then
+    // compensated prefix sums S over valid positions (the group's own
+    // running sum, then base + local for every date with the base's
+    // compensation) into a ring of R >= h + 17 slots, and a mailbox word
+    // (group's first slot, valid bits).  Second thread, one group behind:
+    // the windows W_J = S_J - S_{J-h} (Eq. 3) of the group's monitoring
+    // positions J = n + 1, n + 2, ..., MO_J = W_J / (sigma-hat sqrt(n)),
+    // the test MO_J^2 > lambda^2 log+(J/n) (Eq. 4, squared) and the mean.
+    // The ring can hold one group in flight between the two: the first
+    // thread waits for the second to finish group g - 2 before group g.
     float* ring = reinterpret_cast<float*>(region);  // [P.ring][128]; table B and the A buffers are free now
+    uint32_t* mbox = reinterpret_cast<uint32_t*>(region + (size_t)P.ring * kTile * 4);  // [2][128]
     const int R = P.ring;
     int jm = 0, slot = 0, brk = -1;
     float Sh = 0.f, Sc = 0.f;
@@ -611,6 +638,8 @@ __global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant_
     const float inv_scale = 1.f / scale, lam2 = P.lambda * P.lambda;
     const float lg_n = log2f((float)n_i);
     const int nball = (N + kBlk - 1) / kBlk;
+    uint32_t grp = 0;  // MOSUM group sequence number (the same in both threads)
+    producer = kTile;  // the second threads trail the first ones: refills stay off the first threads' path
     open(d_start / kBlk, nball, N, last);
     for (int d0 = d_start; d0 < P.npad; d0 += kPiece) {
         const int w = P.npad - d0 < kPiece ? P.npad - d0 : kPiece;
@@ -624,80 +653,102 @@ __global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant_
             ptx::mma_commit(bar_done);
         }
         wait_done();
-        if (half == 1) continue;  // (warp-uniform) the second thread of each pair idles here
         const int dend = d0 + w < nball * kBlk ? d0 + w : nball * kBlk;  // whole Y blocks
-        uint32_t rq[8];
-        if (d0 < dend) ptx::tmem_ld8_issue(tmem + lane_base + kColY, rq);
-        const unsigned char* sb = nullptr;
+        if (half == 0) {
+            uint32_t rq[8];
+            if (d0 < dend) ptx::tmem_ld8_issue(tmem + lane_base + kColY, rq);
+            const unsigned char* sb = nullptr;
 #pragma unroll 1
-        for (int c0 = d0; c0 < dend; c0 += 8) {
-            float yc[8], yh[8];
-            const int bd = c0 / kBlk;
-            if ((c0 & 8) == 0) sb = block_wait(bd);
-            const uint32_t vb = read8(sb, c0, yc);
-            if (c0 & 8) block_release(bd, 2);
-            ptx::tmem_wait_ld8(rq);
+            for (int c0 = d0; c0 < dend; c0 += 8, ++grp) {
+                float yc[8], yh[8];
+                const int bd = c0 / kBlk;
+                if ((c0 & 8) == 0) sb = block_wait(bd);
+                const uint32_t vb = read8(sb, c0, yc);
+                if (c0 & 8) block_release(bd, 2);
+                ptx::tmem_wait_ld8(rq);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) yh[e] = __uint_as_float(rq[e]);
-            if (c0 + 8 < dend) ptx::tmem_ld8_issue(tmem + lane_base + kColY + (uint32_t)(c0 + 8 - d0), rq);
-            const int dm = n_hist - c0;  // monitoring dates of the group: e >= dm
-            const uint32_t mon = dm <= 0 ? 0xffu : (dm >= 8 ? 0u : (0xffu << dm) & 0xffu);
-            const uint32_t mv = vb & mon;
-            // prefix sums: the group's own running sum (short, plain), then
-            // S = base + local for every date at once with the base's
-            // compensation (Kahan's correction, applied per date)
-            float loc[8], Sv[8];
-            float acc = 0.f;
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                acc += ((vb >> e) & 1u) ? (yc[e] - yh[e] * inv_b) : 0.f;
-                loc[e] = acc;
-            }
-            float t7 = Sh, c7 = Sc;
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const float yv = loc[e] + Sc;
-                const float tv = Sh + yv;
-                const float cv = yv - (tv - Sh);
-                Sv[e] = tv + cv;
-                if (e == 7) {
-                    t7 = tv;
-                    c7 = cv;
-                }
-            }
-            Sh = t7;
-            Sc = c7;
-            int sl[8];
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int v = (vb >> e) & 1u;
-                if (v) ring[slot * kTile + px] = Sv[e];
-                sl[e] = slot;
-                slot += v;
-                slot = slot == R ? 0 : slot;
-            }
-            if (mon) {  // the same for every thread: a group with monitoring dates
-                uint32_t cross = 0u;
-                float wv[8];
-                int jq = jm;
+                for (int e = 0; e < 8; ++e) yh[e] = __uint_as_float(rq[e]);
+                if (c0 + 8 < dend) ptx::tmem_ld8_issue(tmem + lane_base + kColY + (uint32_t)(c0 + 8 - d0), rq);
+                float loc[8], Sv[8];
+                float acc = 0.f;
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    int ls = sl[e] - h;
-                    ls += ls < 0 ? R : 0;
-                    const float W = Sv[e] - ring[ls * kTile + px];
-                    const float mo = W * inv_scale;
-                    const int J = n_i + jq + 1;
-                    const float b2 = J > jlim ? lam2 * kLn2f * (log2_fast((float)J) - lg_n) : lam2;
-                    const bool mm = (mv >> e) & 1u;
-                    jq += mm ? 1 : 0;
-                    cross |= ((mm && mo * mo > b2) ? 1u : 0u) << e;
-                    wv[e] = mm ? W : 0.f;
+                    acc += ((vb >> e) & 1u) ? (yc[e] - yh[e] * inv_b) : 0.f;
+                    loc[e] = acc;
                 }
-                jm = jq;
-                // the group's windows summed as a tree, then one compensated add
-                const float gsum = ((wv[0] + wv[1]) + (wv[2] + wv[3])) + ((wv[4] + wv[5]) + (wv[6] + wv[7]));
-                comp_add(m0, m0c, gsum);
-                if (brk < 0 && cross) brk = c0 + __ffs(cross) - 1;
+                float t7 = Sh, c7 = Sc;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const float yv = loc[e] + Sc;
+                    const float tv = Sh + yv;
+                    const float cv = yv - (tv - Sh);
+                    Sv[e] = tv + cv;
+                    if (e == 7) {
+                        t7 = tv;
+                        c7 = cv;
+                    }
+                }
+                Sh = t7;
+                Sc = c7;
+                if (grp >= 2) ok &= ptx::mbar_wait_bounded(cons + (grp & 1), ((grp >> 1) - 1u) & 1u, kWaitNs);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    int se = slot + __popc(vb & ((1u << e) - 1u));
+                    se -= se >= R ? R : 0;
+                    if ((vb >> e) & 1u) ring[se * kTile + px] = Sv[e];
+                }
+                mbox[(grp & 1) * kTile + px] = ((uint32_t)slot << 8) | vb;
+                slot += __popc(vb);
+                slot -= slot >= R ? R : 0;
+                mbar_arrive(rdy + (grp & 1));
+            }
+        } else {
+#pragma unroll 1
+            for (int c0 = d0; c0 < dend; c0 += 8, ++grp) {
+                ok &= ptx::mbar_wait_bounded(rdy + (grp & 1), (grp >> 1) & 1u, kWaitNs);
+                const int dm = n_hist - c0;  // monitoring dates of the group: e >= dm
+                const uint32_t mon = dm <= 0 ? 0xffu : (dm >= 8 ? 0u : (0xffu << dm) & 0xffu);
+                if (mon) {  // the same for every thread: a group with monitoring dates
+                    const uint32_t word = mbox[(grp & 1) * kTile + px];
+                    const uint32_t vb = word & 0xffu, mv = vb & mon;
+                    const int sl0 = (int)(word >> 8);
+                    float wv[8], mo2[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        int se = sl0 + __popc(vb & ((1u << e) - 1u));
+                        se -= se >= R ? R : 0;
+                        int ls = se - h;
+                        ls += ls < 0 ? R : 0;
+                        const float W = ring[se * kTile + px] - ring[ls * kTile + px];
+                        const float mo = W * inv_scale;
+                        const bool mm = (mv >> e) & 1u;
+                        wv[e] = mm ? W : 0.f;
+                        mo2[e] = mm ? mo * mo : 0.f;
+                    }
+                    // log+ >= 1: |MO| <= lambda never crosses; the exact boundary
+                    // only for candidates before the first crossing
+                    uint32_t cand = 0u;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) cand |= (mo2[e] > lam2 ? 1u : 0u) << e;
+                    if (brk < 0 && cand) {
+                        int jb = jm;
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            if (brk < 0 && ((cand >> e) & 1u)) {
+                                const int J = n_i + jb + 1;
+                                const float b2 = J > jlim ? lam2 * kLn2f * (log2_fast((float)J) - lg_n) : lam2;
+                                if (mo2[e] > b2) brk = c0 + e;
+                            }
+                            jb += (mv >> e) & 1u;
+                        }
+                    }
+                    jm += __popc(mv);
+                    // the group's windows summed as a tree, then one compensated add
+                    const float gsum = ((wv[0] + wv[1]) + (wv[2] + wv[3])) + ((wv[4] + wv[5]) + (wv[6] + wv[7]));
+                    comp_add(m0, m0c, gsum);
+                }
+                mbar_arrive(cons + (grp & 1));
+                if (tid == producer && (c0 & 8)) block_refill(c0 / kBlk);
             }
         }
     }
@@ -708,7 +759,7 @@ __global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant_
     __syncthreads();
     if (warp == 0) ptx::tmem_dealloc(tmem, kTmemCols);
     if (!__syncthreads_and(ok ? 1 : 0)) ok = false;
-    if (!active || half == 1) return;
+    if (!active || half == 0) return;  // the second thread of the pair holds the MOSUM results
     if (!ok) {
         P.status[p] = BFM_PX_TIMEOUT;
         atomicOr(&g_bfm_mma_err, 2u);
@@ -749,13 +800,13 @@ __global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant_
     }
 }
 
-// Ring of prefix sums: the h slots behind the oldest new position of an
-// 8-date group must survive the group's writes.
+// Ring of prefix sums: the h slots behind the oldest position of the group
+// the second thread reads, that group and the one the first thread writes.
 int ring_len(int n_hist, double h_frac) {
     int hmax = (int)std::floor(h_frac * (double)n_hist);
     if (hmax < 1) hmax = 1;
     if (hmax > n_hist) hmax = n_hist;
-    return hmax + 9;
+    return hmax + 17;
 }
 
 struct MmaLayout {
@@ -771,7 +822,7 @@ MmaLayout mma_layout(int npad, int nhpad, int k, int ring, int elt, bool tma) {
     const size_t ta = (size_t)(npad / 8) * kTabLbo;
     const size_t tb = 3 + 6 * k > 16 ? (size_t)(nhpad / 8) * kTabLbo : 0;
     size_t region = 2 * tb + 2 * (size_t)kBufBytes;
-    const size_t rb = (size_t)ring * kTile * 4;
+    const size_t rb = (size_t)ring * kTile * 4 + 2 * kTile * 4;  // ring and mailbox
     if (rb > region) region = rb;
     region = (region + 1023) & ~(size_t)1023;
     L.region_bytes = (int)region;

@@ -188,7 +188,7 @@ def test_rounding_noise_only_pixels(bfm):
 
 
 def test_bandwidth_limit_is_refused(bfm):
-    """A bandwidth whose MOSUM ring (h + 9 prefix sums per pixel) does not fit
+    """A bandwidth whose MOSUM ring (h + 17 prefix sums per pixel) does not fit
     shared memory next to the tables and the Y stages is BFM_EUNSUPPORTED
     with algo = MMA; AUTO takes the CUDA-core form."""
     d, Y, _ = synth.scene(seed=3, m=256, N=448, n_hist=440, f=23.0, k_gen=3, dtype="i16")
