@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 METRIC = "BFAST-monitor pixels/s at 8.4M px x 414 dates; p50/p99 tile latency"
 # DRAM bytes per pixel per launch from the ncu captures summarised in
 # profiles/ (None once the kernel changes after the capture).
-TRAFFIC_PER_PX = {"f32simt": (1.786e9 / 1048576,), "f32": (None,), "i16": (None,)}
+TRAFFIC_PER_PX = {"f32": (1.786e9 / 1048576,), "f32simt": (None,), "i16": (None,)}
 
 WORKLOAD = "c2: full scene 8,388,608 px x 414 dates, n_hist=228, K=8, f=23, h=0.25, plain float32"
 
@@ -160,6 +160,96 @@ def run_reference(args):
             "e2e": {"value": val, "unit": "pixels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def run_tiles_and_serving(bfm, synth, torch, dev, stream):
+    """c4: 64 uneven int16 tiles (pixel counts rounded up to multiples of 8),
+    each through bfm_monitor (the form AUTO picks) with its own CUDA-event
+    latency, and all of them as one batched persistent launch (CUDA graph,
+    autotuned).  c5: the same tiles served from device memory at Poisson
+    arrival rates 10..500 /s; latency from submission to completion as the
+    server records it."""
+    tiles = []
+    for t in synth.tiles_c4(seed=4, count=64, scale=1.0, px_multiple=8):
+        d, Y, _ = synth.scene_torch(seed=t["seed"], m=t["m"], N=t["N"], n_hist=t["n_hist"], f=23.0, k_gen=t["k"],
+                                    intercept=0.5, slope=0.0, coef_umax=0.3, noise_sd=0.04, miss="markov",
+                                    p_a=t["p_a"], p_b=t["p_b"], break_frac=0.15, step=(-0.5, -0.1), dtype="i16",
+                                    device=dev)
+        design = bfm.Design(d, t["k"], 23.0)
+        tiles.append(dict(t, Y=Y, design=design, lam=synth.lambda_for_horizon(t["N"] / t["n_hist"]),
+                          out=bfm.empty_outputs(2 + 2 * t["k"], t["m"], dev),
+                          mma=bfm.bfm_algo_auto(design, bfm.BFM_I16, t["n_hist"], 0.25, Y, t["m"]) == bfm.BFM_ALGO_MMA))
+    total_px = sum(t["m"] for t in tiles)
+    torch.cuda.synchronize()
+
+    def call(t):
+        o = t["out"]
+        bfm.bfm_monitor_ex(t["design"], t["Y"], bfm.BFM_I16, None, t["m"], t["n_hist"], 0.25, t["lam"],
+                           o["break_idx"], o["mean_mosum"], o["sigma"], o["beta"], o["status"], 0, stream)
+
+    for t in tiles:  # warm-up
+        call(t)
+    torch.cuda.synchronize()
+    lat, tot = [], 0.0
+    for rep in range(3):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(tiles) + 1)]
+        evs[0].record(stream)
+        for i, t in enumerate(tiles):
+            call(t)
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+        per = [evs[i].elapsed_time(evs[i + 1]) for i in range(len(tiles))]
+        lat += per
+        tot += sum(per)
+    lat.sort()
+    c4 = {"workload": "c4: 64 int16 tiles, pixels log-U[1e4, 2e6] rounded up to multiples of 8, N ~ U{120..600}, "
+                      "k ~ U{1..3}, history U(0.4, 0.7), Markov clouds 20-70 %",
+          "pixels": total_px, "tiles_tensor_core_form": sum(t["mma"] for t in tiles),
+          "per_tile_calls": {"value": 3 * total_px / (tot / 1e3), "unit": "pixels/s",
+                             "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1,
+                                            int(math.ceil(0.99 * len(lat))) - 1)], "unit": "one tile"}}}
+    b = bfm.Batch()
+    bouts = []
+    for t in tiles:
+        bouts.append(b.add(t["design"], t["Y"], n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"]))
+    b.autotune(stream)
+    b.run(stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(5):
+        b.run(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    bms = e0.elapsed_time(e1) / 5
+    c4["batched_launch"] = {"value": total_px / (bms / 1e3), "unit": "pixels/s", "ms_per_batch": bms,
+                            "form": "CUDA-core form, one persistent launch replayed from a CUDA graph"}
+    b.close()
+    del bouts
+
+    c5 = {"workload": "c5: the c4 tiles from device memory, Poisson arrivals", "rates": {}}
+    rng = np.random.default_rng(5)
+    for rate in (10, 20, 50, 100, 200, 500):
+        n_req = min(1000, max(50, 2 * rate))
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+        srv = bfm.Server(hbm_budget=32 << 30, slots=4)
+        tickets = []
+        t0 = time.perf_counter()
+        for i, a in enumerate(arrivals):
+            while time.perf_counter() - t0 < a:
+                pass
+            t = tiles[i % len(tiles)]
+            tickets.append(srv.submit(t["design"], t["Y"], n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"]))
+        srv.wait_all(120.0)
+        st = srv.stats()
+        for tk in tickets:
+            srv.release(tk)
+        srv.close()
+        c5["rates"][str(rate)] = {"requests": n_req, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                                  "completed": st["completed"], "pixels_per_s": st["pixels"] / (st["span_ms"] / 1e3)}
+    for t in tiles:
+        t["design"].close()
+    return c4, c5
 
 
 def run_ours(args):
@@ -292,6 +382,13 @@ def run_ours(args):
         cpu = {"value": rate, "unit": "pixels/s", "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count())),
                "kind": "oracle", "sample": f"first {n} pixels of the same scene, all {N} dates, FP64 oracle ({dt:.1f} s)"}
 
+    c4 = c5 = None
+    if not args.no_c4c5:
+        out = wbuf = Y = None  # the c2 scene's device buffers
+        w["Y"] = None
+        torch.cuda.empty_cache()
+        c4, c5 = run_tiles_and_serving(bfm, synth, torch, dev, stream)
+
     line = {
         "metric": METRIC, "value": value, "unit": "pixels/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -304,6 +401,7 @@ def run_ours(args):
         "latency_ms": main["latency_ms"], "roofline": main["roofline"],
         "cpu_baseline": cpu, "e2e": e2e, "clocks": main["clocks"], "gpu_launches": args.steps,
         "forms": {f: {k: v for k, v in r.items() if k != "clocks"} for f, r in res.items()},
+        "c4": c4, "c5": c5,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -322,6 +420,7 @@ def main():
                     help="comma list; the first is the headline (f32 = float storage on tensor cores, "
                          "f32simt = float storage on CUDA cores, i16 = int16 storage on tensor cores)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-c4c5", action="store_true", help="skip the uneven-tile batch and serving legs")
     ap.add_argument("--pixels", type=int, default=None,
                     help="fewer pixels of the same recipe (profiling captures only; not a bench line)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

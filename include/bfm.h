@@ -158,6 +158,11 @@ bfm_status bfm_monitor(bfm_design_t d, const void *Y, int dtype, const uint32_t 
                        int n_hist, double h_frac, double lambda, int32_t *break_idx, float *mean_mosum,
                        float *sigma, float *beta, uint8_t *status, void *stream);
 
+/* The form BFM_ALGO_AUTO takes for these arguments (BFM_ALGO_SIMT or
+ * BFM_ALGO_MMA; no work, no device access).  Y and m matter only through
+ * Y's alignment and m; a NULL or invalid design gives BFM_ALGO_SIMT. */
+int bfm_algo_auto(bfm_design_t d, int dtype, int n_hist, double h_frac, const void *Y, int64_t m);
+
 /* As bfm_monitor with an explicit algorithm (bfm_algo).  BFM_ALGO_MMA needs
  * what BFM_ALGO_AUTO checks for it (else BFM_EUNSUPPORTED). */
 bfm_status bfm_monitor_ex(bfm_design_t d, const void *Y, int dtype, const uint32_t *mask_bits, int64_t m,

@@ -92,6 +92,8 @@ def load(build_if_missing: bool = True):
         lib.bfm_monitor.restype = i32
         lib.bfm_monitor_ex.argtypes = mon + [i32, vp]
         lib.bfm_monitor_ex.restype = i32
+        lib.bfm_algo_auto.argtypes = [vp, i32, i32, dbl, vp, i64]
+        lib.bfm_algo_auto.restype = i32
         lib.bfm_monitor_host_workspace.argtypes = [vp, i32, i64, i32]
         lib.bfm_monitor_host_workspace.restype = sz
         lib.bfm_monitor_host.argtypes = mon + [vp, sz, i64, vp]
@@ -201,6 +203,10 @@ def bfm_monitor_ex(design, Y, dtype, mask_bits, m, n_hist, h_frac, lam, break_id
     _check(load().bfm_monitor_ex(int(design), _ptr(Y), int(dtype), _ptr(mask_bits), int(m), int(n_hist),
                                  float(h_frac), float(lam), _ptr(break_idx), _ptr(mean_mosum), _ptr(sigma),
                                  _ptr(beta), _ptr(status), int(algo), _stream(stream)))
+
+
+def bfm_algo_auto(design, dtype: int, n_hist: int, h_frac: float, Y, m: int) -> int:
+    return load().bfm_algo_auto(int(design), int(dtype), int(n_hist), float(h_frac), _ptr(Y), int(m))
 
 
 def bfm_monitor_host_workspace(design, dtype: int, chunk_px: int, with_mask: bool) -> int:

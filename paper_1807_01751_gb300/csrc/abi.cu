@@ -311,6 +311,11 @@ int bfm_design_K(bfm_design_t d) { return d ? d->K : 0; }
 
 int bfm_design_N(bfm_design_t d) { return d ? d->N : 0; }
 
+int bfm_algo_auto(bfm_design_t d, int dtype, int n_hist, double h_frac, const void* Y, int64_t m) {
+    if (!d || (dtype != BFM_F32 && dtype != BFM_I16) || !(n_hist >= 1 && n_hist < d->N)) return BFM_ALGO_SIMT;
+    return mma_supported(d, dtype, n_hist, h_frac, Y, m, nullptr) ? BFM_ALGO_MMA : BFM_ALGO_SIMT;
+}
+
 bfm_status bfm_monitor_ex(bfm_design_t d, const void* Y, int dtype, const uint32_t* mask_bits, int64_t m, int n_hist,
                           double h_frac, double lambda, int32_t* break_idx, float* mean_mosum, float* sigma,
                           float* beta, uint8_t* status, int algo, void* stream) {

@@ -148,15 +148,17 @@ def workload(name: str, *, m: int | None = None, out_ptr: int | None = None, dty
                 f=w["f"], k=w["k"], h_frac=w["h_frac"], lam=workload_lambda(name), dtype=dt)
 
 
-def tiles_c4(seed: int = 4, count: int = 64, scale: float = 1.0):
+def tiles_c4(seed: int = 4, count: int = 64, scale: float = 1.0, px_multiple: int = 1):
     """Parameters of the uneven-tile batch: pixels log-U[1e4, 2e6] (times
     ``scale``), N ~ U{120..600}, k ~ U{1..3}, history fraction U(0.4, 0.7),
     missing fraction U(0.2, 0.7) as a Markov chain with mean missing run 4
-    (P(missing->clear) = 0.25), int16 storage, h = 0.25."""
+    (P(missing->clear) = 0.25), int16 storage, h = 0.25.  ``px_multiple``
+    rounds the pixel counts up (8: int16 rows of whole 16-byte units)."""
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
         m = int(round(math.exp(rng.uniform(math.log(1e4), math.log(2e6))) * scale))
+        m = -(-m // px_multiple) * px_multiple
         N = int(rng.integers(120, 601))
         k = int(rng.integers(1, 4))
         hf = float(rng.uniform(0.4, 0.7))
