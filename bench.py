@@ -223,7 +223,8 @@ def run_tiles_and_serving(bfm, synth, torch, dev, stream):
     torch.cuda.synchronize()
     bms = e0.elapsed_time(e1) / 5
     c4["batched_launch"] = {"value": total_px / (bms / 1e3), "unit": "pixels/s", "ms_per_batch": bms,
-                            "form": "CUDA-core form, one persistent launch replayed from a CUDA graph"}
+                            "form": "one CUDA-graph replay: persistent tensor-core kernels per (k, storage, "
+                                    "CTAs per SM) group and the persistent CUDA-core kernel"}
     b.close()
     del bouts
 

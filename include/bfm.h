@@ -64,10 +64,11 @@ enum {
 };
 
 /* Algorithm variants for bfm_monitor_ex.  BFM_ALGO_AUTO takes the
- * tensor-core form where it applies (N <= 448 and a MOSUM ring of
- * floor(h_frac * n_hist) + 17 prefix sums per pixel that fits shared memory
- * next to the basis tables: up to about 300 at N = 448), else the CUDA-core
- * form. */
+ * tensor-core form where it applies -- its shared memory (basis tables over
+ * the N dates, a MOSUM ring of floor(h_frac * n_hist) + 17 prefix sums per
+ * pixel, the Y stages) fits one SM, and Y can be described by a tensor map
+ * (16-byte aligned base, m >= 128, rows a multiple of 16 bytes) -- else the
+ * CUDA-core form (bfm_algo_auto tells which). */
 typedef enum {
     BFM_ALGO_AUTO = 0,
     BFM_ALGO_SIMT = 1, /* FP32 CUDA-core path ("plain form") */
@@ -191,10 +192,13 @@ bfm_status bfm_monitor_host(bfm_design_t d, const void *Y_host, int dtype, const
 /*
  * Batched persistent launch -- many scene tiles of uneven pixel counts,
  * series lengths (their own designs), harmonics and storage types processed
- * by ONE kernel launch replayed from a CUDA graph.  The paper processes one
- * scene per call (Algorithm 2); batching is a serving extension with the same
- * per-pixel results: every pixel's outputs equal those of bfm_monitor with
- * BFM_ALGO_SIMT on its tile alone.
+ * by one CUDA-graph replay of persistent kernels: one per tensor-core kernel
+ * variant (k, storage, mask) for the tiles BFM_ALGO_AUTO gives the
+ * tensor-core form (128-pixel blocks), and one CUDA-core kernel for the rest
+ * (32-pixel blocks).  The paper processes one scene per call (Algorithm 2);
+ * batching is a serving extension with the same per-pixel results: every
+ * pixel's outputs equal those of bfm_monitor with BFM_ALGO_AUTO on its tile
+ * alone.
  *   bfm_batch_create    new empty batch on the current device (owned by the
  *                       caller, freed by bfm_batch_destroy).
  *   bfm_batch_add       appends one tile; arguments and errors as
@@ -202,10 +206,11 @@ bfm_status bfm_monitor_host(bfm_design_t d, const void *Y_host, int dtype, const
  *                       alive while the batch runs).  *tile_id (nullable)
  *                       receives its index.  The batch holds a reference to
  *                       the design.
- *   bfm_batch_run       enqueues the whole batch on `stream`: a graph of a
- *                       work-counter reset and the persistent kernel (CTAs =
- *                       SM count x CTAs per SM, taking `grab` 32-pixel blocks
- *                       at a time).  The first run after adds uploads the tile
+ *   bfm_batch_run       enqueues the whole batch on `stream`: a graph of the
+ *                       work-counter resets, the tensor-core kernels (a chain;
+ *                       up to 2 CTAs per SM each) and the CUDA-core kernel (a
+ *                       parallel branch; CTAs = SM count x CTAs per SM, taking
+ *                       `grab` 32-pixel blocks at a time).  The first run after adds uploads the tile
  *                       table and instantiates the graph; later runs replay it.
  *   bfm_batch_autotune  times every (CTAs per SM, grab in {1,2,4,8})
  *                       candidate on this batch (3 replays each, CUDA events on

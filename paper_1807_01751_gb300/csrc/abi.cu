@@ -263,7 +263,7 @@ bfm_status bfm_design_create(const double* dates, int N, int k_harm, double f, b
         return cuda_fail(e, "bfm_design_create: cudaMalloc");
     }
     e = cudaMemcpy(d->d_basis, rows.data(), rows.size() * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && N <= kTcMaxDates) {
+    if (e == cudaSuccess) {
         const int npad = (N + 31) / 32 * 32;  // whole 32-date chunks
         std::vector<unsigned char> tab;
         tc_tables(*d, rowsd, npad, npad, tab);  // table B covers every possible history length
@@ -341,7 +341,7 @@ bfm_status bfm_monitor_ex(bfm_design_t d, const void* Y, int dtype, const uint32
     }
     const bool mma_ok = mma_supported(d, dtype, n_hist, h_frac, Y, m, nullptr);
     if (algo == BFM_ALGO_MMA && !mma_ok) {
-        set_error("bfm_monitor: the tensor-core form needs N <= 448, a MOSUM ring (bandwidth + 17 prefix sums per pixel) that fits shared memory, and Y with a 16-byte aligned base, m >= 128 and rows of a multiple of 16 bytes");
+        set_error("bfm_monitor: the tensor-core form needs basis tables and a MOSUM ring (bandwidth + 17 prefix sums per pixel) that fits shared memory, and Y with a 16-byte aligned base, m >= 128 and rows of a multiple of 16 bytes");
         return BFM_EUNSUPPORTED;
     }
     if (algo == BFM_ALGO_MMA || (algo == BFM_ALGO_AUTO && mma_ok))

@@ -1,14 +1,16 @@
 // Batched persistent launch: many scene tiles of uneven pixel counts, series
-// lengths, harmonics and storage types in ONE kernel launch.
+// lengths, harmonics and storage types in one CUDA-graph replay.
 //
-// The unit of work is a 32-pixel block of some tile.  A grid of persistent
-// CTAs (a multiple of the SM count) takes blocks from a device work counter
-// (atomicAdd, `grab` blocks at a time), finds the owning tile by binary
-// search over the tiles' first-block offsets, and runs the CUDA-core
-// per-pixel path (simt_block) with that tile's parameters and tensor map.
-// The counter reset and the kernel are one CUDA graph, replayed per run.  An
-// autotuner times (CTAs per SM, grab) candidates on the batch itself and
-// keeps the fastest, cached per batch signature.
+// Each tile takes the form bfm_monitor's AUTO would take.  Tensor-core tiles
+// are grouped by kernel variant (k, storage, mask); per variant a persistent
+// grid (up to 2 CTAs per SM) takes 128-pixel blocks from a device counter and
+// finds the owning tile by binary search.  The CUDA-core tiles go to one
+// persistent kernel whose CTAs take 32-pixel blocks, `grab` at a time, in the
+// same way.  The counter resets (one memset node), the tensor-core variants
+// (a chain) and the CUDA-core kernel (a parallel branch) form one graph,
+// instantiated once and replayed.  An autotuner times (CTAs per SM, grab) for
+// the CUDA-core kernel on the batch itself and caches the best pair per batch
+// signature.
 #include <cuda.h>
 
 #include <algorithm>
@@ -34,15 +36,23 @@ bfm_status batch_launch_kernel(const void* tiles, const void* tmaps, int ntiles,
 }  // namespace bfm
 
 struct bfm_batch_s {
+    // CUDA-core tiles
     std::vector<bfm::BatchTileDesc> tiles;
     std::vector<CUtensorMap> tmaps;
-    std::vector<bfm_design_t> designs;  // references held until destroy
     int64_t total_blocks = 0;
     size_t smem = 0;
+    // tensor-core tiles, per group = kernel variant x (2 CTAs per SM or 1)
+    static constexpr int kGroups = 24;
+    std::vector<bfm::MmaBatchTile> mtiles[kGroups];
+    int64_t mblocks[kGroups] = {};
+    size_t msmem[kGroups] = {};
+    int ntiles_all = 0;
+    std::vector<bfm_design_t> designs;  // references held until destroy
     // device copies
     void* d_tiles = nullptr;
     void* d_tmaps = nullptr;
-    unsigned long long* d_counter = nullptr;
+    void* d_mtiles = nullptr;               // all variants, concatenated
+    unsigned long long* d_counter = nullptr;  // [0] CUDA-core kernel, [1 + g] tensor-core group g
     bool dirty = true;
     // launch configuration
     int ctas_per_sm = 0;  // 0 = not tuned yet (use the occupancy maximum)
@@ -82,21 +92,33 @@ void free_dev(bfm_batch_s* b) {
     b->graph = nullptr;
     if (b->d_tiles) cudaFree(b->d_tiles);
     if (b->d_tmaps) cudaFree(b->d_tmaps);
+    if (b->d_mtiles) cudaFree(b->d_mtiles);
     if (b->d_counter) cudaFree(b->d_counter);
-    b->d_tiles = b->d_tmaps = nullptr;
+    b->d_tiles = b->d_tmaps = b->d_mtiles = nullptr;
     b->d_counter = nullptr;
 }
 
 bfm_status upload(bfm_batch_s* b) {
     if (!b->dirty) return BFM_OK;
     free_dev(b);
-    cudaError_t e = cudaMalloc(&b->d_tiles, sizeof(BatchTileDesc) * b->tiles.size());
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_tmaps, sizeof(CUtensorMap) * b->tmaps.size());
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(unsigned long long));
-    if (e == cudaSuccess)
+    size_t nm = 0;
+    for (int v = 0; v < bfm_batch_s::kGroups; ++v) nm += b->mtiles[v].size();
+    cudaError_t e = cudaSuccess;
+    if (!b->tiles.empty()) e = cudaMalloc(&b->d_tiles, sizeof(BatchTileDesc) * b->tiles.size());
+    if (e == cudaSuccess && !b->tmaps.empty()) e = cudaMalloc(&b->d_tmaps, sizeof(CUtensorMap) * b->tmaps.size());
+    if (e == cudaSuccess && nm) e = cudaMalloc(&b->d_mtiles, sizeof(MmaBatchTile) * nm);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, (1 + bfm_batch_s::kGroups) * sizeof(unsigned long long));
+    if (e == cudaSuccess && !b->tiles.empty())
         e = cudaMemcpy(b->d_tiles, b->tiles.data(), sizeof(BatchTileDesc) * b->tiles.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !b->tmaps.empty())
         e = cudaMemcpy(b->d_tmaps, b->tmaps.data(), sizeof(CUtensorMap) * b->tmaps.size(), cudaMemcpyHostToDevice);
+    size_t off = 0;
+    for (int v = 0; v < bfm_batch_s::kGroups && e == cudaSuccess; ++v) {
+        if (b->mtiles[v].empty()) continue;
+        e = cudaMemcpy(static_cast<MmaBatchTile*>(b->d_mtiles) + off, b->mtiles[v].data(),
+                       sizeof(MmaBatchTile) * b->mtiles[v].size(), cudaMemcpyHostToDevice);
+        off += b->mtiles[v].size();
+    }
     if (e != cudaSuccess) return cuda_fail(e, "bfm_batch: uploading tile descriptors");
     b->dirty = false;
     return BFM_OK;
@@ -128,14 +150,31 @@ bfm_status build_graph(bfm_batch_s* b, int grid, int grab) {
     mp.dst = b->d_counter;
     mp.value = 0;
     mp.elementSize = 4;
-    mp.width = 2;
+    mp.width = 2 * (1 + bfm_batch_s::kGroups);  // the counters
     mp.height = 1;
     mp.pitch = 0;
     e = cudaGraphAddMemsetNode(&memset_node, b->graph, nullptr, 0, &mp);
     if (e != cudaSuccess) return cuda_fail(e, "bfm_batch: memset node");
-    bfm_status st = batch_launch_kernel(b->d_tiles, b->d_tmaps, (int)b->tiles.size(), b->total_blocks, b->d_counter,
-                                        grab, grid, b->smem, nullptr, b->graph, &memset_node, &kernel_node);
-    if (st != BFM_OK) return st;
+    bfm_status st = BFM_OK;
+    // tensor-core groups: a chain after the memset
+    cudaGraphNode_t prev = memset_node;
+    size_t off = 0;
+    for (int v = 0; v < bfm_batch_s::kGroups; ++v) {
+        if (b->mtiles[v].empty()) continue;
+        cudaGraphNode_t node;
+        const int mgrid = sm_count(b->device) * mma_ctas_per_sm(b->msmem[v]);
+        st = mma_batch_node(v / 2, static_cast<const MmaBatchTile*>(b->d_mtiles) + off, (int)b->mtiles[v].size(),
+                            b->mblocks[v], b->d_counter + 1 + v, mgrid, b->msmem[v], b->graph, &prev, &node);
+        if (st != BFM_OK) return st;
+        prev = node;
+        off += b->mtiles[v].size();
+    }
+    // CUDA-core tiles: a parallel branch
+    if (!b->tiles.empty() && b->total_blocks > 0) {
+        st = batch_launch_kernel(b->d_tiles, b->d_tmaps, (int)b->tiles.size(), b->total_blocks, b->d_counter, grab,
+                                 grid, b->smem, nullptr, b->graph, &memset_node, &kernel_node);
+        if (st != BFM_OK) return st;
+    }
     e = cudaGraphInstantiate(&b->exec, b->graph, 0);
     if (e != cudaSuccess) return cuda_fail(e, "bfm_batch: graph instantiate");
     b->graph_grid = grid;
@@ -202,6 +241,27 @@ bfm_status bfm_batch_add(bfm_batch_t b, bfm_design_t d, const void* Y, int dtype
         set_error("bfm_batch_add: Y and all outputs must be non-NULL device pointers");
         return BFM_EINVAL;
     }
+    if (m > 0 && mma_supported(d, dtype, n_hist, h_frac, Y, m, nullptr)) {
+        // the tensor-core form, as bfm_monitor's AUTO would take it
+        MmaBatchTile mt;
+        size_t msm = 0;
+        if (!mma_fill_tile(d, dtype, Y, mask_bits, m, n_hist, h_frac, lambda, break_idx, mean_mosum, sigma, beta,
+                           status, &mt, &msm))
+            return BFM_EUNSUPPORTED;
+        // group: kernel variant, and whether two CTAs of this tile share an SM
+        const int v = 2 * mma_variant(d->k, dtype, mask_bits != nullptr) + (mma_ctas_per_sm(msm) == 2 ? 0 : 1);
+        mt.block0 = b->mblocks[v];
+        b->mtiles[v].push_back(mt);
+        b->mblocks[v] += (m + 127) / 128;
+        b->msmem[v] = std::max(b->msmem[v], msm);
+        bfm_design_t dd = nullptr;
+        bfm_design_create(d->dates.data(), d->N, d->k, d->f, &dd);
+        b->designs.push_back(dd);
+        b->dirty = true;
+        if (tile_id) *tile_id = b->ntiles_all;
+        ++b->ntiles_all;
+        return BFM_OK;
+    }
     int br = 0, nb = 0;
     const size_t smem = simt_smem_bytes(d->N, d->k, dtype, &br, &nb);
     if (smem == 0 || smem > 227 * 1024 - 256) {
@@ -244,7 +304,8 @@ bfm_status bfm_batch_add(bfm_batch_t b, bfm_design_t d, const void* Y, int dtype
     bfm_design_create(d->dates.data(), d->N, d->k, d->f, &dd);
     b->designs.push_back(dd);
     b->dirty = true;
-    if (tile_id) *tile_id = (int)b->tiles.size() - 1;
+    if (tile_id) *tile_id = b->ntiles_all;
+    ++b->ntiles_all;
     return BFM_OK;
 }
 
@@ -253,7 +314,7 @@ bfm_status bfm_batch_run(bfm_batch_t b, void* stream) {
         set_error("bfm_batch_run: NULL batch");
         return BFM_EINVAL;
     }
-    if (b->tiles.empty() || b->total_blocks == 0) return BFM_OK;
+    if (b->ntiles_all == 0) return BFM_OK;
     int cps = b->ctas_per_sm;
     if (cps == 0) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -262,7 +323,7 @@ bfm_status bfm_batch_run(bfm_batch_t b, void* stream) {
             cps = it->second.first;
             b->grab = it->second.second;
         } else {
-            cps = max_ctas_per_sm(b->smem);
+            cps = b->tiles.empty() ? 1 : max_ctas_per_sm(b->smem);
         }
     }
     return run_cfg(b, cps, b->grab, (cudaStream_t)stream);
@@ -273,16 +334,19 @@ bfm_status bfm_batch_autotune(bfm_batch_t b, void* stream, int* ctas_per_sm, int
         set_error("bfm_batch_autotune: NULL batch");
         return BFM_EINVAL;
     }
-    if (b->tiles.empty() || b->total_blocks == 0) return BFM_OK;
+    if (b->ntiles_all == 0) return BFM_OK;
     cudaStream_t s = (cudaStream_t)stream;
-    const int maxc = max_ctas_per_sm(b->smem);
+    // only the CUDA-core kernel has choices; without CUDA-core tiles one pair is timed
+    const int maxc = b->tiles.empty() ? 1 : max_ctas_per_sm(b->smem);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
     int bc = maxc, bg = 2;
+    const int ng = b->tiles.empty() ? 1 : 4;
     for (int c = 1; c <= maxc; ++c)
-        for (int g : {1, 2, 4, 8}) {
+        for (int gi = 0; gi < ng; ++gi) {
+            const int g = 1 << gi;
             bfm_status st = run_cfg(b, c, g, s);  // warm-up (and graph build)
             if (st != BFM_OK) {
                 cudaEventDestroy(e0);
@@ -331,6 +395,6 @@ bfm_status bfm_batch_set_config(bfm_batch_t b, int ctas_per_sm, int grab) {
     return BFM_OK;
 }
 
-int bfm_batch_tiles(bfm_batch_t b) { return b ? (int)b->tiles.size() : 0; }
+int bfm_batch_tiles(bfm_batch_t b) { return b ? b->ntiles_all : 0; }
 
 }  // extern "C"

@@ -74,6 +74,50 @@ struct BatchTileDesc {
     int kh, dtype, has_tma, has_mask;
 };
 
+// Parameters of one tile for the tensor-core form (monitor_mma.cu).
+struct MmaParams {
+    const void* Y;
+    const uint32_t* mask;
+    int64_t m, mask_words;
+    int N, n_hist, npad, nhpad;  // npad = N padded to 32, nhpad = n_hist padded to 32
+    int stages;                   // Y blocks in flight
+    int region_bytes;             // table B + A buffers, later the MOSUM ring
+    int vb_extra;                 // bytes of a separate valid-byte area (0: it overlays the delta planes)
+    const uint4* phi;             // A_hi, A_lo, B_hi, B_lo (abi.cu tc_tables), each npad dates long
+    double h_frac;
+    float lambda, c_over_s, inv_s;
+    int ring;
+    int32_t* brk;
+    float* mean;
+    float* sigma;
+    float* beta;
+    uint8_t* status;
+};
+
+// One tile of a batched tensor-core launch (device-side; the tensor map
+// first, so that it sits on a 64-byte boundary in the device table).
+struct MmaBatchTile {
+    CUtensorMap tm;  // 64-byte aligned type
+    MmaParams P;
+    int64_t block0;  // first 128-pixel work block of this tile
+    int kh, dtype, has_mask;
+};
+
+// Fill one batch tile for the tensor-core form (false with a message when the
+// form does not take it); *smem receives the tile's dynamic shared memory.
+bool mma_fill_tile(const bfm_design_s* d, int dtype, const void* Y, const uint32_t* mask, int64_t m, int n_hist,
+                   double h_frac, double lambda, int32_t* brk, float* mean, float* sigma, float* beta,
+                   uint8_t* status, MmaBatchTile* out, size_t* smem);
+// Kernel variant (0..11) of a tile: harmonics k, storage type, explicit mask.
+int mma_variant(int k, int dtype, bool has_mask);
+// Add the persistent tensor-core batch kernel of one variant (its tiles only,
+// block0 numbered within the variant) to `graph` after `dep` (nullable).
+bfm_status mma_batch_node(int variant, const MmaBatchTile* d_tiles, int ntiles, int64_t total_blocks,
+                          unsigned long long* counter, int grid, size_t smem, cudaGraph_t graph,
+                          const cudaGraphNode_t* dep, cudaGraphNode_t* node_out);
+// CTAs of the tensor-core kernel that share one SM at this shared memory (1 or 2).
+int mma_ctas_per_sm(size_t smem);
+
 // Each kernel translation unit keeps its own device error word (bit 0: a
 // tile-load wait gave up); these read and clear it, synchronising `s`.
 cudaError_t simt_read_clear_errors(cudaStream_t s, unsigned int* bits);
@@ -111,7 +155,6 @@ bfm_status launch_simt(const bfm_design_s* d, const void* Y, int dtype, const ui
                        float* beta, uint8_t* status, cudaStream_t stream);
 
 // Tensor-core form: limits and launch.
-constexpr int kTcMaxDates = 448;
 // Basis tables of the tensor-core form (abi.cu tc_tables): table A = basis
 // rows 0..15, table B = rows 16..31, each as fp16 hi then lo, over npad dates.
 // True when the tensor-core form takes these parameters and this Y (a TMA-describable layout).

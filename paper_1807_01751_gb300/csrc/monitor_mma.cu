@@ -74,24 +74,6 @@ constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr uint32_t kALbo = 2048;            // A: K-direction core stride (16 row groups x 128 B)
 constexpr uint32_t kTabLbo = 256;           // B tables: date-group stride (16 rows x 16 B)
 
-struct MmaParams {
-    const void* Y;
-    const uint32_t* mask;
-    int64_t m, mask_words;
-    int N, n_hist, npad, nhpad;  // npad = N padded to 32, nhpad = n_hist padded to 32
-    int stages;                   // Y blocks in flight (TMA loader)
-    int region_bytes;             // table B + A buffers, later the MOSUM ring
-    const uint4* phi;             // A_hi, A_lo, B_hi, B_lo (abi.cu tc_tables), A/B tables npad dates long
-    double h_frac;
-    float lambda, c_over_s, inv_s;
-    int ring;
-    int32_t* brk;
-    float* mean;
-    float* sigma;
-    float* beta;
-    uint8_t* status;
-};
-
 __device__ __forceinline__ uint32_t pack_h2(float a, float b) {
     const __half2 h = __floats2half2_rn(a, b);
     return *reinterpret_cast<const uint32_t*>(&h);
@@ -202,13 +184,19 @@ __device__ __forceinline__ void mbar_arrive_cnt(uint64_t* bar, uint32_t count) {
 // first thread of each pair.
 constexpr int kThreads = 2 * kTile;
 
+constexpr int kHdr = 1024;  // fixed shared-memory header: TMEM address slot, work-block broadcast
+
+// One 128-pixel block `blk` of a tile, on a CTA of kThreads threads that
+// holds kTmemCols TMEM columns at `tmem`; smem_base is the dynamic shared
+// memory (header, then the layout of mma_layout).
 template <int KH, typename T, bool kMask>
-__global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant__ CUtensorMap tmap, const MmaParams P) {
+__device__ __forceinline__ void mma_block(const CUtensorMap* tmap, const MmaParams& P, int64_t blk,
+                                          unsigned char* smem_base, uint32_t tmem) {
     using B = Basis<KH>;
     constexpr int K = B::K, NBR = B::NBR;
     constexpr bool kInt = sizeof(T) == 2;
     constexpr int kStageBytes = kBlk * kTile * (int)sizeof(T);
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem_raw = smem_base + kHdr;
     const size_t ta = (size_t)(P.npad / 8) * kTabLbo, tb = NBR > 16 ? (size_t)(P.nhpad / 8) * kTabLbo : 0;
     unsigned char* tA_hi = smem_raw;
     unsigned char* tA_lo = tA_hi + ta;
@@ -217,24 +205,24 @@ __global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant_
     unsigned char* tB_lo = tB_hi + tb;
     unsigned char* sA = tB_lo + tb;
     unsigned char* sC = region + P.region_bytes;  // beta0 hi, beta0 lo, delta hi, delta lo planes
-    // until the delta planes are written: per-chunk valid bytes [nbh][2][128] and a float per thread
-    unsigned char* sVb = sC + 2 * kCoefPlane;
-    float* sX = reinterpret_cast<float*>(sVb + 28 * 2 * kTile);
     unsigned char* sY = sC + 4 * kCoefPlane;      // Y blocks [16 dates][128 px]
     const int S = P.stages;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(sY + (size_t)S * kStageBytes);
+    // per-chunk valid bytes [nbh][2][128], then a float per thread: in the delta
+    // planes (free until the delta is known) when they fit there, else after the stages
+    unsigned char* sVb = P.vb_extra ? sY + (size_t)S * kStageBytes : sC + 2 * kCoefPlane;
+    float* sX = reinterpret_cast<float*>(sVb + (size_t)((P.n_hist + kBlk - 1) / kBlk) * 2 * kTile);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sY + (size_t)S * kStageBytes + P.vb_extra);
     uint64_t* bar_buf = bars + 0;  // [2] A-buffer reuse
     uint64_t* bar_done = bars + 2;
     uint64_t* full = bars + 3;                 // [S] Y block landed
     uint64_t* empty = bars + 3 + kMaxStages;   // [S] Y block released (256 arrivals)
     uint64_t* rdy = bars + 3 + 2 * kMaxStages;  // [2] MOSUM group published by the first threads
     uint64_t* cons = rdy + 2;                    // [2] MOSUM group consumed by the second threads
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(cons + 2);
-    int* s_dstart = reinterpret_cast<int*>(tslot + 2);
+    int* s_dstart = reinterpret_cast<int*>(cons + 2);
 
     const int tid = threadIdx.x, warp = tid >> 5;
     const int px = tid & (kTile - 1), half = tid >> 7;
-    const int64_t p0 = (int64_t)blockIdx.x * kTile;
+    const int64_t p0 = blk * kTile;
     const int64_t p = p0 + px;
     const bool active = p < P.m;
     const int N = P.N, n_hist = P.n_hist;
@@ -252,9 +240,8 @@ __global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant_
         }
         ptx::fence_mbar_init();
         *s_dstart = N;
-        ptx::prefetch_tmap(&tmap);
+        ptx::prefetch_tmap(tmap);
     }
-    if (warp == 0) ptx::tmem_alloc(tslot, kTmemCols);
     {
         // basis tables: A over all npad dates; B (rows 16..31) over the history
         const uint4* gA = P.phi;
@@ -274,7 +261,6 @@ __global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant_
     ptx::tc_fence_before();
     __syncthreads();
     ptx::tc_fence_after();
-    const uint32_t tmem = *tslot;
     bool ok = true;
 
     const uint64_t keep = l2_policy_evict_last(), last = l2_policy_evict_first();
@@ -293,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant_
         const int st = (int)(q % (uint32_t)S);
         if (q >= (uint32_t)S) ok &= ptx::mbar_wait_bounded(empty + st, ((q / S) - 1u) & 1u, kWaitNs);
         ptx::mbar_arrive_expect_tx(full + st, kStageBytes);
-        tma_load_2d_hint(sY + (size_t)st * kStageBytes, &tmap, full + st, (int)p0, bd * kBlk, s_pol);
+        tma_load_2d_hint(sY + (size_t)st * kStageBytes, tmap, full + st, (int)p0, bd * kBlk, s_pol);
     };
     auto open = [&](int b0, int b1, int tlim, uint64_t pol) {
         s_b0 = b0;
@@ -757,7 +743,6 @@ __global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant_
     // ---- outputs ------------------------------------------------------------------------------
     ptx::tc_fence_before();
     __syncthreads();
-    if (warp == 0) ptx::tmem_dealloc(tmem, kTmemCols);
     if (!__syncthreads_and(ok ? 1 : 0)) ok = false;
     if (!active || half == 0) return;  // the second thread of the pair holds the MOSUM results
     if (!ok) {
@@ -800,6 +785,58 @@ __global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant_
     }
 }
 
+template <int KH, typename T, bool kMask>
+__global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                          const __grid_constant__ MmaParams P) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem);
+    if ((threadIdx.x >> 5) == 0) ptx::tmem_alloc(tslot, kTmemCols);
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = *tslot;
+    mma_block<KH, T, kMask>(&tmap, P, (int64_t)blockIdx.x, smem, tmem);
+    ptx::tc_fence_before();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) ptx::tmem_dealloc(tmem, kTmemCols);
+}
+
+// Persistent form over a batch of tiles of one (k, storage, mask) variant:
+// CTAs take 128-pixel blocks from a device counter, find the owning tile by
+// binary search over the tiles' first-block numbers and run mma_block with
+// its parameters and tensor map.
+template <int KH, typename T, bool kMask>
+__global__ void __launch_bounds__(kThreads, 2) mma_batch_kernel(const MmaBatchTile* __restrict__ tiles, int ntiles,
+                                                                int64_t total_blocks,
+                                                                unsigned long long* counter) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem);
+    long long* s_blk = reinterpret_cast<long long*>(smem + 8);
+    if ((threadIdx.x >> 5) == 0) ptx::tmem_alloc(tslot, kTmemCols);
+    ptx::tc_fence_before();
+    __syncthreads();
+    ptx::tc_fence_after();
+    const uint32_t tmem = *tslot;
+    while (true) {
+        if (threadIdx.x == 0) *s_blk = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const int64_t blk = *s_blk;
+        __syncthreads();  // read by all before thread 0 takes the next one
+        if (blk >= total_blocks) break;
+        int lo = 0, hi = ntiles - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tiles[mid].block0 <= blk) lo = mid;
+            else hi = mid - 1;
+        }
+        const MmaBatchTile* t = tiles + lo;
+        mma_block<KH, T, kMask>(&t->tm, t->P, blk - t->block0, smem, tmem);
+    }
+    ptx::tc_fence_before();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) ptx::tmem_dealloc(tmem, kTmemCols);
+}
+
 // Ring of prefix sums: the h slots behind the oldest position of the group
 // the second thread reads, that group and the one the first thread writes.
 int ring_len(int n_hist, double h_frac) {
@@ -810,7 +847,7 @@ int ring_len(int n_hist, double h_frac) {
 }
 
 struct MmaLayout {
-    int stages, region_bytes;
+    int stages, region_bytes, vb_extra;
     size_t smem;
 };
 
@@ -827,7 +864,12 @@ MmaLayout mma_layout(int npad, int nhpad, int k, int ring, int elt, bool tma) {
     region = (region + 1023) & ~(size_t)1023;
     L.region_bytes = (int)region;
     L.stages = tma ? (elt == 4 ? 3 : 6) : 0;
-    L.smem = 2 * ta + region + 4 * (size_t)kCoefPlane + (size_t)L.stages * kBlk * kTile * elt + 256;
+    // valid bytes (2 per history block and pixel) and the pair exchange floats
+    const int nbh = (nhpad + kBlk - 1) / kBlk;
+    const size_t vb = (size_t)nbh * 2 * kTile + 2 * kTile * 4;
+    L.vb_extra = vb <= 2 * (size_t)kCoefPlane ? 0 : (int)((vb + 127) & ~(size_t)127);
+    L.smem = kHdr + 2 * ta + region + 4 * (size_t)kCoefPlane + (size_t)L.stages * kBlk * kTile * elt + L.vb_extra +
+             256;
     return L;
 }
 
@@ -873,7 +915,7 @@ bool mma_layout_ok(const void* Y, int dtype, int64_t m) {
 
 bool mma_supported(const bfm_design_s* d, int dtype, int n_hist, double h_frac, const void* Y, int64_t m,
                    size_t* smem_out) {
-    if ((dtype != BFM_I16 && dtype != BFM_F32) || !d->d_phi_tc || d->N > kTcMaxDates) return false;
+    if ((dtype != BFM_I16 && dtype != BFM_F32) || !d->d_phi_tc) return false;
     if (!mma_layout_ok(Y, dtype, m)) return false;
     const MmaLayout L = mma_layout(d->npad_tc, (n_hist + 31) / 32 * 32, d->k, ring_len(n_hist, h_frac),
                                    dtype == BFM_F32 ? 4 : 2, true);
@@ -881,11 +923,24 @@ bool mma_supported(const bfm_design_s* d, int dtype, int n_hist, double h_frac, 
     return L.smem <= 227 * 1024;
 }
 
-bfm_status launch_mma(const bfm_design_s* d, int dtype, const void* Y, const uint32_t* mask, int64_t m,
-                      int n_hist, double h_frac, double lambda, int32_t* brk, float* mean, float* sigma,
-                      float* beta, uint8_t* status, cudaStream_t stream) {
-    if (m == 0) return BFM_OK;
+namespace {
+
+// P, the tensor map and the shared memory of one tile (false, with a message,
+// when the tensor-core form does not take it).
+bool mma_prepare(const bfm_design_s* d, int dtype, const void* Y, const uint32_t* mask, int64_t m, int n_hist,
+                 double h_frac, double lambda, int32_t* brk, float* mean, float* sigma, float* beta,
+                 uint8_t* status, MmaParams* Pout, CUtensorMap* tm, size_t* smem_out) {
     const int elt = dtype == BFM_F32 ? 4 : 2;
+    if (!mma_supported(d, dtype, n_hist, h_frac, Y, m, nullptr) || m < kTile) {
+        set_error("tensor-core form: needs basis tables and a MOSUM ring that fit shared memory, and Y with a "
+                  "16-byte aligned base, m >= 128 and rows of a multiple of 16 bytes");
+        return false;
+    }
+    auto enc = encode_fn_mma();
+    if (!enc) {
+        set_error("tensor-core form: cuTensorMapEncodeTiled is not available");
+        return false;
+    }
     MmaParams P{};
     P.Y = Y;
     P.mask = mask;
@@ -906,38 +961,104 @@ bfm_status launch_mma(const bfm_design_s* d, int dtype, const void* Y, const uin
     P.sigma = sigma;
     P.beta = beta;
     P.status = status;
-    CUtensorMap tm;
-    std::memset(&tm, 0, sizeof tm);
-    auto enc = encode_fn_mma();
-    if (!mma_layout_ok(Y, dtype, m) || !enc) {
-        set_error("tensor-core form: Y needs a 16-byte aligned base, m >= 128 and rows of a multiple of 16 bytes");
-        return BFM_EUNSUPPORTED;
-    }
-    {
-        cuuint64_t gdim[2] = {(cuuint64_t)m, (cuuint64_t)d->N};
-        cuuint64_t gstride[1] = {(cuuint64_t)m * elt};
-        cuuint32_t box[2] = {(cuuint32_t)kTile, (cuuint32_t)kBlk};
-        cuuint32_t es[2] = {1u, 1u};
-        const CUresult r = enc(&tm, elt == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 2,
-                               const_cast<void*>(Y), gdim, gstride, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) {
-            set_error("tensor-core form: cuTensorMapEncodeTiled failed for Y");
-            return BFM_EUNSUPPORTED;
-        }
+    std::memset(tm, 0, sizeof *tm);
+    cuuint64_t gdim[2] = {(cuuint64_t)m, (cuuint64_t)d->N};
+    cuuint64_t gstride[1] = {(cuuint64_t)m * elt};
+    cuuint32_t box[2] = {(cuuint32_t)kTile, (cuuint32_t)kBlk};
+    cuuint32_t es[2] = {1u, 1u};
+    const CUresult r = enc(tm, elt == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 2,
+                           const_cast<void*>(Y), gdim, gstride, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("tensor-core form: cuTensorMapEncodeTiled failed for Y");
+        return false;
     }
     const MmaLayout L = mma_layout(P.npad, P.nhpad, d->k, P.ring, elt, true);
     P.stages = L.stages;
     P.region_bytes = L.region_bytes;
+    P.vb_extra = L.vb_extra;
     // At least 80 KB, so that at most two CTAs (2 x 256 TMEM columns) share an SM.
-    size_t smem = L.smem < 80 * 1024 ? 80 * 1024 : L.smem;
+    *smem_out = L.smem < 80 * 1024 ? 80 * 1024 : L.smem;
+    *Pout = P;
+    return true;
+}
+
+}  // namespace
+
+bfm_status launch_mma(const bfm_design_s* d, int dtype, const void* Y, const uint32_t* mask, int64_t m,
+                      int n_hist, double h_frac, double lambda, int32_t* brk, float* mean, float* sigma,
+                      float* beta, uint8_t* status, cudaStream_t stream) {
+    if (m == 0) return BFM_OK;
+    MmaParams P;
+    CUtensorMap tm;
+    size_t smem = 0;
+    if (!mma_prepare(d, dtype, Y, mask, m, n_hist, h_frac, lambda, brk, mean, sigma, beta, status, &P, &tm, &smem))
+        return BFM_EUNSUPPORTED;
     const bool i16 = dtype == BFM_I16;
     switch (d->k) {
         case 1: return i16 ? launch_t<1, int16_t>(tm, P, smem, stream) : launch_t<1, float>(tm, P, smem, stream);
         case 2: return i16 ? launch_t<2, int16_t>(tm, P, smem, stream) : launch_t<2, float>(tm, P, smem, stream);
         default: return i16 ? launch_t<3, int16_t>(tm, P, smem, stream) : launch_t<3, float>(tm, P, smem, stream);
     }
+}
+
+bool mma_fill_tile(const bfm_design_s* d, int dtype, const void* Y, const uint32_t* mask, int64_t m, int n_hist,
+                   double h_frac, double lambda, int32_t* brk, float* mean, float* sigma, float* beta,
+                   uint8_t* status, MmaBatchTile* out, size_t* smem) {
+    std::memset(out, 0, sizeof *out);
+    if (!mma_prepare(d, dtype, Y, mask, m, n_hist, h_frac, lambda, brk, mean, sigma, beta, status, &out->P, &out->tm,
+                     smem))
+        return false;
+    out->kh = d->k;
+    out->dtype = dtype;
+    out->has_mask = mask != nullptr;
+    return true;
+}
+
+int mma_ctas_per_sm(size_t smem) { return smem + 1024 <= 114 * 1024 ? 2 : 1; }
+
+namespace {
+template <int KH, typename T, bool kMask>
+void* batch_kernel_fn() {
+    return (void*)mma_batch_kernel<KH, T, kMask>;
+}
+}  // namespace
+
+int mma_variant(int k, int dtype, bool has_mask) { return ((k - 1) * 2 + (dtype == BFM_I16 ? 1 : 0)) * 2 + (has_mask ? 1 : 0); }
+
+bfm_status mma_batch_node(int variant, const MmaBatchTile* d_tiles, int ntiles, int64_t total_blocks,
+                          unsigned long long* counter, int grid, size_t smem, cudaGraph_t graph,
+                          const cudaGraphNode_t* dep, cudaGraphNode_t* node_out) {
+    static void* const fns[12] = {
+        batch_kernel_fn<1, float, false>(),   batch_kernel_fn<1, float, true>(),
+        batch_kernel_fn<1, int16_t, false>(), batch_kernel_fn<1, int16_t, true>(),
+        batch_kernel_fn<2, float, false>(),   batch_kernel_fn<2, float, true>(),
+        batch_kernel_fn<2, int16_t, false>(), batch_kernel_fn<2, int16_t, true>(),
+        batch_kernel_fn<3, float, false>(),   batch_kernel_fn<3, float, true>(),
+        batch_kernel_fn<3, int16_t, false>(), batch_kernel_fn<3, int16_t, true>()};
+    if (variant < 0 || variant >= 12) {
+        set_error("bfm_batch: bad tensor-core variant");
+        return BFM_EINVAL;
+    }
+    static thread_local int configured[12] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (configured[variant] != dev) {
+        cudaError_t e = cudaFuncSetAttribute(fns[variant], cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(mma_batch_kernel)");
+        configured[variant] = dev;
+    }
+    void* args[] = {(void*)&d_tiles, (void*)&ntiles, (void*)&total_blocks, (void*)&counter};
+    cudaKernelNodeParams kp{};
+    kp.func = fns[variant];
+    kp.gridDim = dim3((unsigned)grid);
+    kp.blockDim = dim3(kThreads);
+    kp.sharedMemBytes = (unsigned)smem;
+    kp.kernelParams = args;
+    const cudaError_t e = cudaGraphAddKernelNode(node_out, graph, dep, dep ? 1 : 0, &kp);
+    if (e != cudaSuccess) return cuda_fail(e, "bfm_batch: tensor-core kernel node");
+    return BFM_OK;
 }
 
 }  // namespace bfm

@@ -20,9 +20,9 @@ def bfm():
     return bfm
 
 
-def _tiles(scale=0.01, count=10):
+def _tiles(scale=0.01, count=10, px_multiple=1):
     out = []
-    for t in synth.tiles_c4(seed=4, count=count, scale=scale):
+    for t in synth.tiles_c4(seed=4, count=count, scale=scale, px_multiple=px_multiple):
         d, Y, _ = synth.scene(seed=t["seed"], m=t["m"], N=t["N"], n_hist=t["n_hist"], f=23.0, k_gen=t["k"],
                               intercept=0.5, slope=0.0, coef_umax=0.3, noise_sd=0.04, miss="markov", p_a=t["p_a"],
                               p_b=t["p_b"], break_frac=0.15, step=(-0.5, -0.1),
@@ -40,7 +40,7 @@ def test_batch_equals_single_calls_and_oracle(bfm):
         d = bfm.Design(t["dates"], t["k"], 23.0)
         Yd = torch.from_numpy(t["Y"]).cuda()
         outs.append(b.add(d, Yd, n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"]))
-        singles.append(bfm.monitor(d, Yd, n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"], algo=bfm.BFM_ALGO_SIMT))
+        singles.append(bfm.monitor(d, Yd, n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"], algo=bfm.BFM_ALGO_AUTO))
     b.run()
     torch.cuda.synchronize()
     assert bfm.bfm_device_errors() == 0
@@ -55,6 +55,34 @@ def test_batch_equals_single_calls_and_oracle(bfm):
         ref = oracle.monitor(t["dates"], Ys, k=t["k"], f=23.0, n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"])
         rep = compare(g, ref, t["dates"], t["k"], 23.0, tol=1e-5 if t["Y"].dtype == np.float32 else 1e-4)
         assert rep["ok"], (t["tile"], rep)
+    b.close()
+
+
+def test_batch_tensor_core_variants(bfm):
+    """Tiles of every harmonic order in both storage types, widths rounded to
+    multiples of 8 so that AUTO gives them the tensor-core form: the
+    persistent tensor-core kernels (one per variant) reproduce single calls
+    bit for bit."""
+    tiles = _tiles(scale=0.02, count=16, px_multiple=8)
+    b = bfm.Batch()
+    outs, singles, forms = [], [], set()
+    for t in tiles:
+        d = bfm.Design(t["dates"], t["k"], 23.0)
+        Yd = torch.from_numpy(t["Y"]).cuda()
+        dt = bfm.BFM_F32 if t["Y"].dtype == np.float32 else bfm.BFM_I16
+        if bfm.bfm_algo_auto(d, dt, t["n_hist"], 0.25, Yd, t["m"]) == bfm.BFM_ALGO_MMA:
+            forms.add((t["k"], dt))
+        outs.append(b.add(d, Yd, n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"]))
+        singles.append(bfm.monitor(d, Yd, n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"]))
+    assert len(forms) >= 4, forms
+    b.run()
+    b.run()
+    torch.cuda.synchronize()
+    assert bfm.bfm_device_errors() == 0
+    for o, sgl in zip(outs, singles):
+        a, c = to_numpy(o), to_numpy(sgl)
+        for key in a:
+            np.testing.assert_array_equal(a[key].view(np.uint8), c[key].view(np.uint8))
     b.close()
 
 

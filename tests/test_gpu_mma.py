@@ -127,9 +127,10 @@ def test_mask_bits(bfm):
 
 
 @pytest.mark.parametrize("dtype", ["i16", "f32"])
-@pytest.mark.parametrize("k,N,n_hist", [(1, 150, 70), (2, 300, 180), (3, 448, 340), (1, 61, 37)])
+@pytest.mark.parametrize("k,N,n_hist", [(1, 150, 70), (2, 300, 180), (3, 448, 340), (1, 61, 37), (3, 600, 420),
+                                         (1, 1000, 500)])
 def test_harmonics_and_lengths(bfm, k, N, n_hist, dtype):
-    """Each harmonic order, 61 to 448 dates.  (Short series with many
+    """Each harmonic order, 61 to 1000 dates (one CTA per SM from about 450).  (Short series with many
     regressors, e.g. K = 8 from 17 history dates at 55 % clouds, give Gram
     condition numbers up to 1e9 below the singularity threshold: no FP32 form
     meets 1e-4 there, so they are not parity cases.)"""
@@ -198,6 +199,18 @@ def test_bandwidth_limit_is_refused(bfm):
     g = _run(bfm, d, Y, k=3, n_hist=440, h_frac=1.0, lam=1.75, algo=0)
     # windows over the whole history: FP32 sums of ~180 residuals per window
     _check(d, Y, g, k=3, n_hist=440, h_frac=1.0, lam=1.75)
+
+
+def test_tables_beyond_shared_memory_are_refused(bfm):
+    """1792 dates with k = 3 and a long history: the basis tables alone exceed
+    an SM's shared memory, so AUTO takes the CUDA-core form."""
+    d, Y, _ = synth.scene(seed=5, m=256, N=1792, n_hist=1600, f=23.0, k_gen=3, dtype="i16")
+    design = bfm.Design(d, 3, 23.0)
+    Yd = torch.from_numpy(Y).cuda()
+    assert bfm.bfm_algo_auto(design, bfm.BFM_I16, 1600, 0.25, Yd, 256) == bfm.BFM_ALGO_SIMT
+    with pytest.raises(bfm.BfmError) as ei:
+        _run(bfm, d, Y, k=3, n_hist=1600, h_frac=0.25, lam=1.75)
+    assert ei.value.code == 6
 
 
 def test_wide_bandwidth(bfm):
