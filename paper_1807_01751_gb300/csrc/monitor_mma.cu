@@ -606,9 +606,10 @@ __device__ __forceinline__ void mma_block(const CUtensorMap* tmap, const MmaPara
     // First thread of the pair: yhat = X beta0 + X delta per kPiece-date TMEM
     // piece (the fp16 split error of beta0 lies in the span of X and cancels
     // against the refinement); per 8-date group the residuals, then
-    // compensated prefix sums S over valid positions (the group's own
-    // running sum, then base + local for every date with the base's
-    // compensation) into a ring of R >= h + 17 slots, and a mailbox word
+    // prefix sums S over valid positions (the group's own running sum, then
+    // S = base_hi + (base_lo + local) for every date, the base carried as an
+    // unevaluated sum and advanced by one TwoSum per group) into a ring of
+    // R >= h + 17 slots, and a mailbox word
     // (group's first slot, valid bits).  Second thread, one group behind:
     // the windows W_J = S_J - S_{J-h} (Eq. 3) of the group's monitoring
     // positions J = n + 1, n + 2, ..., MO_J = W_J / (sigma-hat sqrt(n)),
@@ -662,26 +663,30 @@ __device__ __forceinline__ void mma_block(const CUtensorMap* tmap, const MmaPara
                     acc += ((vb >> e) & 1u) ? (yc[e] - yh[e] * inv_b) : 0.f;
                     loc[e] = acc;
                 }
-                float t7 = Sh, c7 = Sc;
+                // the base is the unevaluated sum Sh + Sc: each S is rounded once
+                // from it, and the base moves on by one TwoSum per group
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const float yv = loc[e] + Sc;
-                    const float tv = Sh + yv;
-                    const float cv = yv - (tv - Sh);
-                    Sv[e] = tv + cv;
-                    if (e == 7) {
-                        t7 = tv;
-                        c7 = cv;
-                    }
+                for (int e = 0; e < 8; ++e) Sv[e] = Sh + (Sc + loc[e]);
+                {
+                    const float b = Sc + loc[7];
+                    const float t = Sh + b;
+                    const float bv = t - Sh;
+                    Sc = (Sh - (t - bv)) + (b - bv);
+                    Sh = t;
                 }
-                Sh = t7;
-                Sc = c7;
                 if (grp >= 2) ok &= ptx::mbar_wait_bounded(cons + (grp & 1), ((grp >> 1) - 1u) & 1u, kWaitNs);
+                if (slot <= R - 8) {  // the group's slots do not wrap
+                    float* wp = ring + slot * kTile + px;
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    int se = slot + __popc(vb & ((1u << e) - 1u));
-                    se -= se >= R ? R : 0;
-                    if ((vb >> e) & 1u) ring[se * kTile + px] = Sv[e];
+                    for (int e = 0; e < 8; ++e)
+                        if ((vb >> e) & 1u) wp[__popc(vb & ((1u << e) - 1u)) * kTile] = Sv[e];
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) {
+                        int se = slot + __popc(vb & ((1u << e) - 1u));
+                        se -= se >= R ? R : 0;
+                        if ((vb >> e) & 1u) ring[se * kTile + px] = Sv[e];
+                    }
                 }
                 mbox[(grp & 1) * kTile + px] = ((uint32_t)slot << 8) | vb;
                 slot += __popc(vb);
@@ -699,12 +704,16 @@ __device__ __forceinline__ void mma_block(const CUtensorMap* tmap, const MmaPara
                     const uint32_t vb = word & 0xffu, mv = vb & mon;
                     const int sl0 = (int)(word >> 8);
                     float wv[8], mo2[8];
+                    const bool nowrap = sl0 <= R - 8 && sl0 >= h;  // neither the slots nor their lags wrap
 #pragma unroll
                     for (int e = 0; e < 8; ++e) {
                         int se = sl0 + __popc(vb & ((1u << e) - 1u));
-                        se -= se >= R ? R : 0;
                         int ls = se - h;
-                        ls += ls < 0 ? R : 0;
+                        if (!nowrap) {
+                            se -= se >= R ? R : 0;
+                            ls = se - h;
+                            ls += ls < 0 ? R : 0;
+                        }
                         const float W = ring[se * kTile + px] - ring[ls * kTile + px];
                         const float mo = W * inv_scale;
                         const bool mm = (mv >> e) & 1u;
