@@ -383,6 +383,16 @@ def run_ours(args):
         cpu = {"value": rate, "unit": "pixels/s", "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count())),
                "kind": "oracle", "sample": f"first {n} pixels of the same scene, all {N} dates, FP64 oracle ({dt:.1f} s)"}
 
+    # critical value of Eq. 4 by simulation (c2's alpha, h and N/n): 1e5 paths, 1000 steps per unit
+    lam_sim = None
+    if rank == 0:
+        t0 = time.perf_counter()
+        lam_v = bfm.bfm_lambda(0.05, 0.25, N / n_hist, G=1000, reps=100000, seed=12345, stream=stream)
+        lam_ms = (time.perf_counter() - t0) * 1e3
+        lam_sim = {"alpha": 0.05, "h": 0.25, "T": N / n_hist, "grid_per_unit": 1000, "paths": 100000,
+                   "lambda": lam_v, "ms": lam_ms, "paths_per_s": 1e5 / (lam_ms / 1e3),
+                   "note": "bfm_lambda, one FP64 path per thread, host quantile; wall time of the call"}
+
     c4 = c5 = None
     if not args.no_c4c5:
         out = wbuf = Y = None  # the c2 scene's device buffers
@@ -402,7 +412,7 @@ def run_ours(args):
         "latency_ms": main["latency_ms"], "roofline": main["roofline"],
         "cpu_baseline": cpu, "e2e": e2e, "clocks": main["clocks"], "gpu_launches": args.steps,
         "forms": {f: {k: v for k, v in r.items() if k != "clocks"} for f, r in res.items()},
-        "c4": c4, "c5": c5,
+        "c4": c4, "c5": c5, "lambda_simulation": lam_sim,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

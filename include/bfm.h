@@ -159,6 +159,26 @@ bfm_status bfm_monitor(bfm_design_t d, const void *Y, int dtype, const uint32_t 
                        int n_hist, double h_frac, double lambda, int32_t *break_idx, float *mean_mosum,
                        float *sigma, float *beta, uint8_t *status, void *stream);
 
+/*
+ * bfm_lambda -- the critical value lambda(alpha, h, N/n) of the boundary
+ * lambda*sqrt(log+(t)) (Eq. 4), found by simulation of the limiting process
+ * as the paper prescribes (Section 2.3; Section 4.3 prints 2.39 for
+ * alpha = 0.05, h = 0.5, N/n = 2).  `reps` Brownian paths on a grid of G
+ * steps per unit time up to T = N/n (T * G steps, rounded), one per GPU
+ * thread, each from its own SplitMix64 stream (path r: state
+ * seed * 0xA0761D6478BD642F + r * 0xE7037ED1A0B428DB + 1, one draw
+ * discarded) with Box-Muller normals; the statistic of a path is
+ * sup over t = i/G in [1, T] of |W(t) - W(t-h) - h W(1)| / sqrt(log+ t),
+ * with h rounded to whole steps.  *lambda_out receives the
+ * ceil((1 - alpha) * reps)-th smallest statistic; stats_host (nullable,
+ * host, reps doubles) receives all of them.  Runs on `stream` and returns
+ * when done (synchronising it).  FP64 arithmetic.
+ * Errors: BFM_EINVAL (0 < alpha < 1, 0 < h <= 1, T > 1, G >= 1, reps >= 1
+ * and round(h * G) >= 1 are required), BFM_ECUDA.
+ */
+bfm_status bfm_lambda(double alpha, double h, double T, int G, int reps, uint64_t seed, double *lambda_out,
+                      double *stats_host, void *stream);
+
 /* The form BFM_ALGO_AUTO takes for these arguments (BFM_ALGO_SIMT or
  * BFM_ALGO_MMA; no work, no device access).  Y and m matter only through
  * Y's alignment and m; a NULL or invalid design gives BFM_ALGO_SIMT. */

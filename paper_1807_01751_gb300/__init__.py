@@ -94,6 +94,8 @@ def load(build_if_missing: bool = True):
         lib.bfm_monitor_ex.restype = i32
         lib.bfm_algo_auto.argtypes = [vp, i32, i32, dbl, vp, i64]
         lib.bfm_algo_auto.restype = i32
+        lib.bfm_lambda.argtypes = [dbl, dbl, dbl, i32, i32, ctypes.c_uint64, ctypes.POINTER(dbl), vp, vp]
+        lib.bfm_lambda.restype = i32
         lib.bfm_monitor_host_workspace.argtypes = [vp, i32, i64, i32]
         lib.bfm_monitor_host_workspace.restype = sz
         lib.bfm_monitor_host.argtypes = mon + [vp, sz, i64, vp]
@@ -203,6 +205,18 @@ def bfm_monitor_ex(design, Y, dtype, mask_bits, m, n_hist, h_frac, lam, break_id
     _check(load().bfm_monitor_ex(int(design), _ptr(Y), int(dtype), _ptr(mask_bits), int(m), int(n_hist),
                                  float(h_frac), float(lam), _ptr(break_idx), _ptr(mean_mosum), _ptr(sigma),
                                  _ptr(beta), _ptr(status), int(algo), _stream(stream)))
+
+
+def bfm_lambda(alpha: float, h: float, T: float, G: int = 1000, reps: int = 100000, seed: int = 12345,
+               return_stats: bool = False, stream=None):
+    """Critical value lambda(alpha, h, T) of Eq. 4 by simulation on the GPU
+    (see include/bfm.h); with return_stats also the per-path statistics."""
+    import numpy as np
+    lam = ctypes.c_double(0.0)
+    stats = np.empty(int(reps), dtype=np.float64) if return_stats else None
+    _check(load().bfm_lambda(float(alpha), float(h), float(T), int(G), int(reps), ctypes.c_uint64(int(seed)),
+                             ctypes.byref(lam), stats.ctypes.data if stats is not None else None, _stream(stream)))
+    return (lam.value, stats) if return_stats else lam.value
 
 
 def bfm_algo_auto(design, dtype: int, n_hist: int, h_frac: float, Y, m: int) -> int:
