@@ -159,6 +159,16 @@ bfm_status bfm_monitor(bfm_design_t d, const void *Y, int dtype, const uint32_t 
                        int n_hist, double h_frac, double lambda, int32_t *break_idx, float *mean_mosum,
                        float *sigma, float *beta, uint8_t *status, void *stream);
 
+/* As bfm_monitor_ex with one more output: max_mosum (device, nullable,
+ * float [m]) receives for each pixel the MO_j of largest magnitude over its
+ * monitoring positions (signed; the first of equal magnitudes) -- the map of
+ * maximum absolute MOSUM values of Section 4.3 (Chile scene).  0 for
+ * BFM_PX_DEGENERATE, NaN for the other statuses without a fit or without
+ * monitoring data. */
+bfm_status bfm_monitor_ext(bfm_design_t d, const void *Y, int dtype, const uint32_t *mask_bits, int64_t m,
+                           int n_hist, double h_frac, double lambda, int32_t *break_idx, float *mean_mosum,
+                           float *sigma, float *beta, uint8_t *status, float *max_mosum, int algo, void *stream);
+
 /*
  * bfm_lambda -- the critical value lambda(alpha, h, N/n) of the boundary
  * lambda*sqrt(log+(t)) (Eq. 4), found by simulation of the limiting process

@@ -155,6 +155,24 @@ def monitor(dates, Y, *, k: int, f: float, n_hist: int, h_frac: float, lam: floa
     return out
 
 
+def max_mosum(out: dict) -> np.ndarray:
+    """From monitor(..., trace=True): per pixel the MO of largest magnitude
+    over the monitoring positions (signed, the first of equal magnitudes), 0
+    for DEGENERATE, NaN for pixels without a fit or without monitoring data
+    (the map of maximum absolute MOSUM values, Section 4.3)."""
+    tr = out["mo_trace"]
+    m = tr.shape[0]
+    res = np.full(m, np.nan)
+    for p in range(m):
+        st = out["status"][p]
+        if st == 3:
+            res[p] = 0.0
+        elif st == 0:
+            row = tr[p][~np.isnan(tr[p])]
+            res[p] = row[int(np.argmax(np.abs(row)))]
+    return res
+
+
 def critical_value(alpha: float, h: float, T: float, *, G: int = 1000, reps: int = 100000,
                    seed: int = 12345, return_stats: bool = False):
     """lambda(alpha, h, T) as the (1-alpha) quantile of the simulated supremum

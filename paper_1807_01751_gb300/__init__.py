@@ -92,6 +92,8 @@ def load(build_if_missing: bool = True):
         lib.bfm_monitor.restype = i32
         lib.bfm_monitor_ex.argtypes = mon + [i32, vp]
         lib.bfm_monitor_ex.restype = i32
+        lib.bfm_monitor_ext.argtypes = mon + [vp, i32, vp]
+        lib.bfm_monitor_ext.restype = i32
         lib.bfm_algo_auto.argtypes = [vp, i32, i32, dbl, vp, i64]
         lib.bfm_algo_auto.restype = i32
         lib.bfm_lambda.argtypes = [dbl, dbl, dbl, i32, i32, ctypes.c_uint64, ctypes.POINTER(dbl), vp, vp]
@@ -223,6 +225,13 @@ def bfm_algo_auto(design, dtype: int, n_hist: int, h_frac: float, Y, m: int) -> 
     return load().bfm_algo_auto(int(design), int(dtype), int(n_hist), float(h_frac), _ptr(Y), int(m))
 
 
+def bfm_monitor_ext(design, Y, dtype, mask_bits, m, n_hist, h_frac, lam, break_idx, mean_mosum, sigma, beta,
+                    status, max_mosum, algo, stream=None):
+    _check(load().bfm_monitor_ext(int(design), _ptr(Y), int(dtype), _ptr(mask_bits), int(m), int(n_hist),
+                                  float(h_frac), float(lam), _ptr(break_idx), _ptr(mean_mosum), _ptr(sigma),
+                                  _ptr(beta), _ptr(status), _ptr(max_mosum), int(algo), _stream(stream)))
+
+
 def bfm_monitor_host_workspace(design, dtype: int, chunk_px: int, with_mask: bool) -> int:
     return load().bfm_monitor_host_workspace(int(design), int(dtype), int(chunk_px), int(bool(with_mask)))
 
@@ -328,16 +337,23 @@ def empty_outputs(K: int, m: int, device="cuda"):
 
 
 def monitor(design: Design, Y, *, n_hist: int, h_frac: float, lam: float, mask_bits=None, out=None,
-            algo: int = BFM_ALGO_AUTO, stream=None):
-    """Run bfm_monitor_ex on a device tensor Y [N][m] (float32 or int16)."""
+            algo: int = BFM_ALGO_AUTO, stream=None, max_mosum: bool = False):
+    """Run bfm_monitor_ex (bfm_monitor_ext with max_mosum=True: one more
+    output, "max_mosum") on a device tensor Y [N][m] (float32 or int16)."""
     import torch
     assert Y.is_cuda and Y.dim() == 2 and Y.is_contiguous()
     dtype = {torch.float32: BFM_F32, torch.int16: BFM_I16}[Y.dtype]
     m = Y.shape[1]
     if out is None:
         out = empty_outputs(design.K, m, Y.device)
-    bfm_monitor_ex(design, Y, dtype, mask_bits, m, n_hist, h_frac, lam, out["break_idx"], out["mean_mosum"],
-                   out["sigma"], out["beta"], out["status"], algo, stream)
+    if max_mosum:
+        if "max_mosum" not in out:
+            out["max_mosum"] = torch.empty(m, dtype=torch.float32, device=Y.device)
+        bfm_monitor_ext(design, Y, dtype, mask_bits, m, n_hist, h_frac, lam, out["break_idx"], out["mean_mosum"],
+                        out["sigma"], out["beta"], out["status"], out["max_mosum"], algo, stream)
+    else:
+        bfm_monitor_ex(design, Y, dtype, mask_bits, m, n_hist, h_frac, lam, out["break_idx"], out["mean_mosum"],
+                       out["sigma"], out["beta"], out["status"], algo, stream)
     return out
 
 

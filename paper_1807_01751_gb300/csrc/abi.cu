@@ -316,9 +316,9 @@ int bfm_algo_auto(bfm_design_t d, int dtype, int n_hist, double h_frac, const vo
     return mma_supported(d, dtype, n_hist, h_frac, Y, m, nullptr) ? BFM_ALGO_MMA : BFM_ALGO_SIMT;
 }
 
-bfm_status bfm_monitor_ex(bfm_design_t d, const void* Y, int dtype, const uint32_t* mask_bits, int64_t m, int n_hist,
-                          double h_frac, double lambda, int32_t* break_idx, float* mean_mosum, float* sigma,
-                          float* beta, uint8_t* status, int algo, void* stream) {
+bfm_status bfm_monitor_ext(bfm_design_t d, const void* Y, int dtype, const uint32_t* mask_bits, int64_t m,
+                           int n_hist, double h_frac, double lambda, int32_t* break_idx, float* mean_mosum,
+                           float* sigma, float* beta, uint8_t* status, float* max_mosum, int algo, void* stream) {
     if (!valid_common(d, dtype, m, n_hist, h_frac, lambda, "bfm_monitor")) return BFM_EINVAL;
     if (m == 0) return BFM_OK;
     if (!Y || !break_idx || !mean_mosum || !sigma || !beta || !status) {
@@ -346,9 +346,16 @@ bfm_status bfm_monitor_ex(bfm_design_t d, const void* Y, int dtype, const uint32
     }
     if (algo == BFM_ALGO_MMA || (algo == BFM_ALGO_AUTO && mma_ok))
         return launch_mma(d, dtype, Y, mask_bits, m, n_hist, h_frac, lambda, break_idx, mean_mosum, sigma, beta, status,
-                          (cudaStream_t)stream);
+                          (cudaStream_t)stream, max_mosum);
     return launch_simt(d, Y, dtype, mask_bits, m, n_hist, h_frac, lambda, break_idx, mean_mosum, sigma, beta, status,
-                       (cudaStream_t)stream);
+                       (cudaStream_t)stream, max_mosum);
+}
+
+bfm_status bfm_monitor_ex(bfm_design_t d, const void* Y, int dtype, const uint32_t* mask_bits, int64_t m, int n_hist,
+                          double h_frac, double lambda, int32_t* break_idx, float* mean_mosum, float* sigma,
+                          float* beta, uint8_t* status, int algo, void* stream) {
+    return bfm_monitor_ext(d, Y, dtype, mask_bits, m, n_hist, h_frac, lambda, break_idx, mean_mosum, sigma, beta,
+                           status, nullptr, algo, stream);
 }
 
 bfm_status bfm_monitor(bfm_design_t d, const void* Y, int dtype, const uint32_t* mask_bits, int64_t m, int n_hist,

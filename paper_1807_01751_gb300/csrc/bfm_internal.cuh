@@ -65,6 +65,7 @@ struct MonitorParams {
     float* sigma;
     float* beta;              // [K][m]
     uint8_t* status;
+    float* maxmo;             // nullable: MO of largest magnitude per pixel
 };
 
 // One tile of a batched launch (device-side descriptor).
@@ -92,6 +93,7 @@ struct MmaParams {
     float* sigma;
     float* beta;
     uint8_t* status;
+    float* maxmo;  // nullable: MO of largest magnitude per pixel
 };
 
 // One tile of a batched tensor-core launch (device-side; the tensor map
@@ -152,7 +154,7 @@ bfm_status cuda_fail(cudaError_t e, const char* what);
 // Launch the CUDA-core (SIMT) kernel for one tile set on `stream`.
 bfm_status launch_simt(const bfm_design_s* d, const void* Y, int dtype, const uint32_t* mask, int64_t m,
                        int n_hist, double h_frac, double lambda, int32_t* brk, float* mean, float* sigma,
-                       float* beta, uint8_t* status, cudaStream_t stream);
+                       float* beta, uint8_t* status, cudaStream_t stream, float* maxmo = nullptr);
 
 // Tensor-core form: limits and launch.
 // Basis tables of the tensor-core form (abi.cu tc_tables): table A = basis
@@ -162,7 +164,7 @@ bool mma_supported(const bfm_design_s* d, int dtype, int n_hist, double h_frac, 
                    size_t* smem_out);
 bfm_status launch_mma(const bfm_design_s* d, int dtype, const void* Y, const uint32_t* mask, int64_t m,
                       int n_hist, double h_frac, double lambda, int32_t* brk, float* mean, float* sigma,
-                      float* beta, uint8_t* status, cudaStream_t stream);
+                      float* beta, uint8_t* status, cudaStream_t stream, float* maxmo = nullptr);
 cudaError_t mma_read_clear_errors(cudaStream_t s, unsigned int* bits);
 
 // Shared-memory bytes the SIMT kernel needs for N dates, k harmonics and a dtype (0 if too large).

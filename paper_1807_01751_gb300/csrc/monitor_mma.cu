@@ -622,6 +622,8 @@ __device__ __forceinline__ void mma_block(const CUtensorMap* tmap, const MmaPara
     int jm = 0, slot = 0, brk = -1;
     float Sh = 0.f, Sc = 0.f;
     float m0 = 0.f, m0c = 0.f;
+    float mx = 0.f;  // MO of largest magnitude (the first of equals), when asked for
+    const bool want_mx = P.maxmo != nullptr;
     const float inv_scale = 1.f / scale, lam2 = P.lambda * P.lambda;
     const float lg_n = log2f((float)n_i);
     const int nball = (N + kBlk - 1) / kBlk;
@@ -737,6 +739,11 @@ __device__ __forceinline__ void mma_block(const CUtensorMap* tmap, const MmaPara
                             jb += (mv >> e) & 1u;
                         }
                     }
+                    if (want_mx) {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            if (((mv >> e) & 1u) && mo2[e] > mx * mx) mx = wv[e] * inv_scale;
+                    }
                     jm += __popc(mv);
                     // the group's windows summed as a tree, then one compensated add
                     const float gsum = ((wv[0] + wv[1]) + (wv[2] + wv[3])) + ((wv[4] + wv[5]) + (wv[6] + wv[7]));
@@ -785,6 +792,7 @@ __device__ __forceinline__ void mma_block(const CUtensorMap* tmap, const MmaPara
     P.brk[p] = o_brk;
     P.mean[p] = o_mean;
     P.sigma[p] = o_sigma;
+    if (want_mx) P.maxmo[p] = st == BFM_PX_OK ? mx : (st == BFM_PX_DEGENERATE ? 0.f : qnan);
 #pragma unroll
     for (int i = 0; i < K; ++i) {
         float bi = beta[i];
@@ -938,7 +946,7 @@ namespace {
 // when the tensor-core form does not take it).
 bool mma_prepare(const bfm_design_s* d, int dtype, const void* Y, const uint32_t* mask, int64_t m, int n_hist,
                  double h_frac, double lambda, int32_t* brk, float* mean, float* sigma, float* beta,
-                 uint8_t* status, MmaParams* Pout, CUtensorMap* tm, size_t* smem_out) {
+                 uint8_t* status, float* maxmo, MmaParams* Pout, CUtensorMap* tm, size_t* smem_out) {
     const int elt = dtype == BFM_F32 ? 4 : 2;
     if (!mma_supported(d, dtype, n_hist, h_frac, Y, m, nullptr) || m < kTile) {
         set_error("tensor-core form: needs basis tables and a MOSUM ring that fit shared memory, and Y with a "
@@ -970,6 +978,7 @@ bool mma_prepare(const bfm_design_s* d, int dtype, const void* Y, const uint32_t
     P.sigma = sigma;
     P.beta = beta;
     P.status = status;
+    P.maxmo = maxmo;
     std::memset(tm, 0, sizeof *tm);
     cuuint64_t gdim[2] = {(cuuint64_t)m, (cuuint64_t)d->N};
     cuuint64_t gstride[1] = {(cuuint64_t)m * elt};
@@ -997,12 +1006,13 @@ bool mma_prepare(const bfm_design_s* d, int dtype, const void* Y, const uint32_t
 
 bfm_status launch_mma(const bfm_design_s* d, int dtype, const void* Y, const uint32_t* mask, int64_t m,
                       int n_hist, double h_frac, double lambda, int32_t* brk, float* mean, float* sigma,
-                      float* beta, uint8_t* status, cudaStream_t stream) {
+                      float* beta, uint8_t* status, cudaStream_t stream, float* maxmo) {
     if (m == 0) return BFM_OK;
     MmaParams P;
     CUtensorMap tm;
     size_t smem = 0;
-    if (!mma_prepare(d, dtype, Y, mask, m, n_hist, h_frac, lambda, brk, mean, sigma, beta, status, &P, &tm, &smem))
+    if (!mma_prepare(d, dtype, Y, mask, m, n_hist, h_frac, lambda, brk, mean, sigma, beta, status, maxmo, &P, &tm,
+                     &smem))
         return BFM_EUNSUPPORTED;
     const bool i16 = dtype == BFM_I16;
     switch (d->k) {
@@ -1016,8 +1026,8 @@ bool mma_fill_tile(const bfm_design_s* d, int dtype, const void* Y, const uint32
                    double h_frac, double lambda, int32_t* brk, float* mean, float* sigma, float* beta,
                    uint8_t* status, MmaBatchTile* out, size_t* smem) {
     std::memset(out, 0, sizeof *out);
-    if (!mma_prepare(d, dtype, Y, mask, m, n_hist, h_frac, lambda, brk, mean, sigma, beta, status, &out->P, &out->tm,
-                     smem))
+    if (!mma_prepare(d, dtype, Y, mask, m, n_hist, h_frac, lambda, brk, mean, sigma, beta, status, nullptr, &out->P,
+                     &out->tm, smem))
         return false;
     out->kh = d->k;
     out->dtype = dtype;

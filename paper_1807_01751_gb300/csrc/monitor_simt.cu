@@ -210,6 +210,7 @@ __device__ __forceinline__ void simt_block(const CUtensorMap* tmap, const Monito
             P.brk[p] = o.brk;
             P.mean[p] = o.mean;
             P.sigma[p] = o.sigma;
+            if (P.maxmo) P.maxmo[p] = o.maxmo;
 #pragma unroll
             for (int i = 0; i < K; ++i) P.beta[(size_t)i * P.m + p] = o.beta[i];
         }
@@ -353,7 +354,7 @@ size_t simt_smem_bytes(int N, int k, int dtype, int* box_rows, int* nbox) {
 
 bfm_status launch_simt(const bfm_design_s* d, const void* Y, int dtype, const uint32_t* mask, int64_t m, int n_hist,
                        double h_frac, double lambda, int32_t* brk, float* mean, float* sigma, float* beta,
-                       uint8_t* status, cudaStream_t stream) {
+                       uint8_t* status, cudaStream_t stream, float* maxmo) {
     MonitorParams P{};
     int br = 0, nb = 0;
     size_t smem = simt_smem_bytes(d->N, d->k, dtype, &br, &nb);
@@ -379,6 +380,7 @@ bfm_status launch_simt(const bfm_design_s* d, const void* Y, int dtype, const ui
     P.sigma = sigma;
     P.beta = beta;
     P.status = status;
+    P.maxmo = maxmo;
 
     CUtensorMap tm;
     memset(&tm, 0, sizeof(tm));

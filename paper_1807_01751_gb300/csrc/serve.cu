@@ -25,10 +25,6 @@
 
 namespace bfm {
 
-bfm_status launch_simt(const bfm_design_s* d, const void* Y, int dtype, const uint32_t* mask, int64_t m, int n_hist,
-                       double h_frac, double lambda, int32_t* brk, float* mean, float* sigma, float* beta,
-                       uint8_t* status, cudaStream_t stream);
-
 namespace {
 
 double now_ms() {

@@ -179,7 +179,8 @@ constexpr int kSegWords = 14;
 template <int KH>
 struct Partials {
     static constexpr int kGram = Basis<KH>::NBR + Basis<KH>::K + 1;
-    static constexpr int kStride = kGram > 3 + kSegWords ? kGram : 3 + kSegWords;
+    static constexpr int kMaxMo = 3 + kSegWords;  // phase 7: the segment's MO of largest magnitude
+    static constexpr int kStride = kGram > kMaxMo + 1 ? kGram : kMaxMo + 1;
 };
 
 // Per-lane state carried across phases (registers on the device).
@@ -428,6 +429,7 @@ __host__ __device__ __forceinline__ void phase7_mosum(const SegParams& P, int w,
         }
     int first = -1;
     float mh = 0.f, ml = 0.f;
+    float mx = 0.f;  // MO of largest magnitude in this segment (the first of equals)
     for (int jl = jlo; jl < jhi; ++jl) {
         const int J = off + jl + 1;  // 1-based valid position
         if (jl < mycnt && J > n_i) {
@@ -452,19 +454,21 @@ __host__ __device__ __forceinline__ void phase7_mosum(const SegParams& P, int w,
             const float mo = W * S.inv_scale;
             const float b2 = J > S.jlim ? S.lam2 * kLn2f * (log2_fast((float)J) - S.lg_n) : S.lam2;
             if (first < 0 && mo * mo > b2) first = jl;
+            if (fabsf(mo) > fabsf(mx)) mx = mo;
             comp_add(mh, ml, W);
         }
     }
     part(w, 0) = first < 0 ? -1.f : (float)(s0 + nth_valid(w, first, (s1 - s0 + 31) >> 5, getw));
     part(w, 1) = mh;
     part(w, 2) = ml;
+    part(w, Partials<KH>::kMaxMo) = mx;
 }
 
 template <int KH>
 struct PixelOut {
     uint8_t status;
     int32_t brk;
-    float mean, sigma;
+    float mean, sigma, maxmo;
     float beta[Basis<KH>::K];
 };
 
@@ -474,13 +478,15 @@ __host__ __device__ __forceinline__ void phase8_out(const SegParams& P, const La
                                                     PixelOut<KH>& o) {
     constexpr int K = Basis<KH>::K;
     int brk = -1;
-    float mh = 0.f, ml = 0.f;
+    float mh = 0.f, ml = 0.f, mx = 0.f;
 #pragma unroll
     for (int w = 0; w < kNW; ++w) {
         const float f = part(w, 0);
         if (brk < 0 && f >= 0.f) brk = (int)f;
         comp_add(mh, ml, part(w, 1));
         ml += part(w, 2);
+        const float x = part(w, Partials<KH>::kMaxMo);
+        if (fabsf(x) > fabsf(mx)) mx = x;  // segments in date order: the first of equals
     }
     const int n_i = S.n_i, N_i = S.N_i;
     const bool degenerate = !(S.sigma > kDegenerateRatio * S.ymax) || S.ymax == 0.f;
@@ -497,17 +503,21 @@ __host__ __device__ __forceinline__ void phase8_out(const SegParams& P, const La
     } else if (degenerate) {
         o.status = BFM_PX_DEGENERATE;
         o.mean = 0.f;
+        o.maxmo = 0.f;
     } else if (N_i == n_i) {
         o.status = BFM_PX_NO_MONITOR;
         o.mean = qnan;
+        o.maxmo = qnan;
     } else {
         o.status = BFM_PX_OK;
         o.brk = brk;
         o.mean = (mh + ml) / ((float)(N_i - n_i) * S.scale);
+        o.maxmo = mx;
     }
     if (!fitted) {
         o.mean = qnan;
         o.sigma = qnan;
+        o.maxmo = qnan;
     }
     // beta of the centred trend -> raw parameterisation of Eq. 2
 #pragma unroll

@@ -217,3 +217,34 @@ def test_c2_full_scene_properties(c2_full, algo):
     tb = w["true_break"]
     det = (b >= 0)
     assert det[tb >= 0].mean() > 0.8
+
+
+@pytest.mark.parametrize("dtype", ["f32", "i16"])
+@ALGOS
+def test_max_mosum(bfm, algo, dtype):
+    """bfm_monitor_ext's map of the largest-magnitude MO (Section 4.3) against
+    the oracle's MO trace: magnitudes within the form's tolerance, the sign
+    wherever the runner-up magnitude is not within 1e-4 of the largest (the
+    first of near-equal values may differ by rounding)."""
+    w = synth.workload("c1" if dtype == "f32" else "c3", m=1024)
+    d = bfm.Design(w["dates"], 3, 23.0)
+    Yd = torch.from_numpy(w["Y"]).cuda()
+    out = bfm.monitor(d, Yd, n_hist=w["n_hist"], h_frac=w["h_frac"], lam=w["lam"], algo=algo, max_mosum=True)
+    torch.cuda.synchronize()
+    assert bfm.bfm_device_errors() == 0
+    g = out["max_mosum"].cpu().numpy().astype(np.float64)
+    ref = oracle.monitor(w["dates"], w["Y"], k=3, f=23.0, n_hist=w["n_hist"], h_frac=w["h_frac"], lam=w["lam"],
+                         trace=True)
+    r = oracle.max_mosum(ref)
+    st = out["status"].cpu().numpy()
+    assert (st == ref["status"]).all()
+    assert (np.isnan(g) == np.isnan(r)).all()
+    ok = ~np.isnan(r)
+    tol = 1e-5 if dtype == "f32" else 1e-4
+    err = np.abs(np.abs(g[ok]) - np.abs(r[ok])) / np.maximum(1.0, np.abs(r[ok]))
+    print("max |max_mosum| error", err.max())
+    assert err.max() < tol
+    tr = np.abs(np.nan_to_num(ref["mo_trace"], nan=0.0))
+    srt = np.sort(tr, axis=1)
+    clear = ok & (srt[:, -1] - srt[:, -2] > 1e-4 * np.maximum(1.0, srt[:, -1]))
+    assert (np.sign(g[clear]) == np.sign(r[clear])).all()

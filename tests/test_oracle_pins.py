@@ -330,3 +330,24 @@ def test_trend_extrapolation_inflates_null_crossings():
         rates.append((o["break_idx"] >= 0).mean())
     assert 0.01 < rates[0] < 0.12
     assert rates[1] > 2 * rates[0]
+
+
+def test_max_mosum_definition():
+    """max_mosum is the signed MO of largest magnitude over the monitoring
+    positions: a downward step gives a negative value whose magnitude is the
+    largest |MO| of the trace; DEGENERATE gives 0, too little history NaN."""
+    w = synth.workload("c1", m=256)
+    Y = w["Y"].copy()
+    n = w["n_hist"]
+    Y[n + 10:, 1] -= 0.5                                  # strong downward step
+    Y[:, 2] = np.float32(0.25)                            # constant: DEGENERATE
+    Y[6:n, 3] = np.nan                                    # too little history
+    out = oracle.monitor(w["dates"], Y, k=3, f=23.0, n_hist=n, h_frac=0.25, lam=w["lam"], trace=True)
+    mx = oracle.max_mosum(out)
+    tr = out["mo_trace"]
+    assert out["status"][1] == 0 and mx[1] < 0
+    assert mx[1] == np.nanmin(tr[1]) and abs(mx[1]) == np.nanmax(np.abs(tr[1]))
+    assert out["status"][2] == 3 and mx[2] == 0.0
+    assert out["status"][3] == 1 and np.isnan(mx[3])
+    ok = out["status"] == 0
+    assert np.all(np.abs(mx[ok]) == np.nanmax(np.abs(tr[ok]), axis=1))
