@@ -189,6 +189,39 @@ bfm_status bfm_monitor_ext(bfm_design_t d, const void *Y, int dtype, const uint3
 bfm_status bfm_lambda(double alpha, double h, double T, int G, int reps, uint64_t seed, double *lambda_out,
                       double *stats_host, void *stream);
 
+/*
+ * bfm_trace -- residuals and MOSUM process of selected pixels, for the
+ * examination of individual series once the breaks are known (Section 3.2,
+ * after Algorithm 2: the device path returns only the breaks, the
+ * intermediate results of chosen series are looked at afterwards).
+ * One warp per selected pixel redoes the pixel's fit in FP64 (Eq. 5-6 by
+ * Cholesky on the normal equations of the Eq. 2 regressors, trend centred
+ * and scaled), then writes, indexed by the ORIGINAL date t:
+ *   resid[i*N + t]  y_t - x_t'beta (Eq. 3 sign) where date t is valid, NaN
+ *                   where it is missing;
+ *   mo[i*N + t]     MO_j of Eq. 3 where date t is the valid monitoring
+ *                   observation at position j (j > n_p), NaN elsewhere
+ *                   (history and missing dates); sigma-hat with n_p - K
+ *                   degrees of freedom, h_p = clamp(floor(h_frac * n_p), 1,
+ *                   n_p) as in bfm_monitor.
+ * Arguments: d, Y, dtype, mask_bits, m, n_hist, h_frac as for bfm_monitor
+ * (the same values the statuses came from); pixels (device, nullable)
+ * int64 [count] pixel indices in 0..m-1 (NULL: pixels 0..count-1);
+ * status (device) uint8 [m], the status array bfm_monitor wrote for these
+ * data -- only pixels with status OK, DEGENERATE or NO_MONITOR have a fit,
+ * the rows of the others (and of an index outside 0..m-1) are all NaN, and
+ * DEGENERATE pixels get MO = 0 at their monitoring dates; mo and resid
+ * (device, each nullable but not both) float [count][N], caller-owned.
+ * Asynchronous on `stream`; no workspace.  Each selected pixel's column of
+ * Y is read with one gather per date, so this is meant for the pixels of
+ * interest, not for whole scenes.
+ * Errors: BFM_EINVAL (arguments as listed), BFM_EUNSUPPORTED (count above
+ * 2^31 - 1 warps' worth), BFM_ECUDA.
+ */
+bfm_status bfm_trace(bfm_design_t d, const void *Y, int dtype, const uint32_t *mask_bits, int64_t m, int n_hist,
+                     double h_frac, const int64_t *pixels, int64_t count, const uint8_t *status, float *mo,
+                     float *resid, void *stream);
+
 /* The form BFM_ALGO_AUTO takes for these arguments (BFM_ALGO_SIMT or
  * BFM_ALGO_MMA; no work, no device access).  Y and m matter only through
  * Y's alignment and m; a NULL or invalid design gives BFM_ALGO_SIMT. */

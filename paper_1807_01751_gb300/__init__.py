@@ -98,6 +98,8 @@ def load(build_if_missing: bool = True):
         lib.bfm_algo_auto.restype = i32
         lib.bfm_lambda.argtypes = [dbl, dbl, dbl, i32, i32, ctypes.c_uint64, ctypes.POINTER(dbl), vp, vp]
         lib.bfm_lambda.restype = i32
+        lib.bfm_trace.argtypes = [vp, vp, i32, vp, i64, i32, dbl, vp, i64, vp, vp, vp, vp]
+        lib.bfm_trace.restype = i32
         lib.bfm_monitor_host_workspace.argtypes = [vp, i32, i64, i32]
         lib.bfm_monitor_host_workspace.restype = sz
         lib.bfm_monitor_host.argtypes = mon + [vp, sz, i64, vp]
@@ -219,6 +221,11 @@ def bfm_lambda(alpha: float, h: float, T: float, G: int = 1000, reps: int = 1000
     _check(load().bfm_lambda(float(alpha), float(h), float(T), int(G), int(reps), ctypes.c_uint64(int(seed)),
                              ctypes.byref(lam), stats.ctypes.data if stats is not None else None, _stream(stream)))
     return (lam.value, stats) if return_stats else lam.value
+
+
+def bfm_trace(design, Y, dtype, mask_bits, m, n_hist, h_frac, pixels, count, status, mo, resid, stream=None):
+    _check(load().bfm_trace(int(design), _ptr(Y), int(dtype), _ptr(mask_bits), int(m), int(n_hist), float(h_frac),
+                            _ptr(pixels), int(count), _ptr(status), _ptr(mo), _ptr(resid), _stream(stream)))
 
 
 def bfm_algo_auto(design, dtype: int, n_hist: int, h_frac: float, Y, m: int) -> int:
@@ -354,6 +361,29 @@ def monitor(design: Design, Y, *, n_hist: int, h_frac: float, lam: float, mask_b
     else:
         bfm_monitor_ex(design, Y, dtype, mask_bits, m, n_hist, h_frac, lam, out["break_idx"], out["mean_mosum"],
                        out["sigma"], out["beta"], out["status"], algo, stream)
+    return out
+
+
+def trace(design: Design, Y, *, n_hist: int, h_frac: float, status, pixels=None, count=None, mask_bits=None,
+          resid: bool = True, stream=None):
+    """bfm_trace on a device tensor Y [N][m]: for the pixels (int64 device
+    tensor, or the first `count` pixels) the MOSUM process "mo" and, with
+    resid=True, the residuals "resid", each [count][N] float32 indexed by
+    the original date (NaN where undefined).  `status` is the status output
+    of monitor() on the same data."""
+    import torch
+    assert Y.is_cuda and Y.dim() == 2 and Y.is_contiguous()
+    dtype = {torch.float32: BFM_F32, torch.int16: BFM_I16}[Y.dtype]
+    N, m = Y.shape
+    if pixels is not None:
+        assert pixels.is_cuda and pixels.dtype == torch.int64 and pixels.is_contiguous()
+        count = pixels.numel()
+    count = int(count)
+    out = dict(mo=torch.empty((count, N), dtype=torch.float32, device=Y.device))
+    if resid:
+        out["resid"] = torch.empty((count, N), dtype=torch.float32, device=Y.device)
+    bfm_trace(design, Y, dtype, mask_bits, m, n_hist, h_frac, pixels, count, status, out["mo"], out.get("resid"),
+              stream)
     return out
 
 

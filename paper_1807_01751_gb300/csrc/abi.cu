@@ -271,9 +271,14 @@ bfm_status bfm_design_create(const double* dates, int N, int k_harm, double f, b
         if (e == cudaSuccess) e = cudaMemcpy(d->d_phi_tc, tab.data(), tab.size(), cudaMemcpyHostToDevice);
         d->npad_tc = npad;
     }
+    if (e == cudaSuccess) {
+        e = cudaMalloc(&d->d_dates, sizeof(double) * (size_t)N);
+        if (e == cudaSuccess) e = cudaMemcpy(d->d_dates, dates, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         cudaFree(d->d_basis);
         if (d->d_phi_tc) cudaFree(d->d_phi_tc);
+        if (d->d_dates) cudaFree(d->d_dates);
         delete d;
         return cuda_fail(e, "bfm_design_create: device tables");
     }
@@ -297,6 +302,7 @@ bfm_status bfm_design_destroy(bfm_design_t d) {
                 if (cur != d->device) cudaSetDevice(d->device);
                 cudaFree(d->d_basis);
                 if (d->d_phi_tc) cudaFree(d->d_phi_tc);
+                if (d->d_dates) cudaFree(d->d_dates);
                 if (cur != d->device) cudaSetDevice(cur);
                 delete d;
             }

@@ -136,6 +136,7 @@ struct bfm_design_s {
     double c = 0.0, s = 1.0;  // trend centring/scaling
     int NB = 0;               // basis row stride (floats)
     float* d_basis = nullptr; // device [N][NB]
+    double* d_dates = nullptr; // device [N]: the date values (bfm_trace)
     // Tensor-core B operands: the basis table as fp16 hi and lo parts in the
     // no-swizzle core-matrix layout (see abi.cu tc_tables); nullptr when N
     // exceeds the tensor-core limit.

@@ -77,3 +77,59 @@ def compare(gpu: dict, ref: dict, dates, k: int, f: float, *, tol: float, margin
 
 def to_numpy(out: dict) -> dict:
     return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+EPS_OUT = 2.0 ** -23  # two roundings to float
+
+
+def check_trace_rows(sel, mo, rs, ref, vals, valid, X, lam, *, m):
+    """bfm_trace rows (mo, rs: [len(sel)][N]; rs may be None) against the
+    oracle's results (ref from oracle.monitor(..., trace=True) plus
+    ref["n_hist"]; vals/valid from oracle.valid_and_values; X the raw Eq. 2
+    design) for the pixels `sel`, indices into ref's pixels (outside 0..m-1:
+    rows of NaN).  MO by monitoring position is mapped to the original dates;
+    reference residuals are y - x'beta with the oracle's beta.  Tolerance: the
+    float rounding of the output plus 1e-9 relative (both sides FP64).
+    Returns (worst MO error, worst residual error / max|y|, breaks checked)."""
+    worst_mo = worst_r = 0.0
+    checked_breaks = 0
+    for row, p in enumerate(sel):
+        if p < 0 or p >= m:
+            assert np.isnan(mo[row]).all() and (rs is None or np.isnan(rs[row]).all())
+            continue
+        st = ref["status"][p]
+        if st in (1, 2):
+            assert np.isnan(mo[row]).all() and (rs is None or np.isnan(rs[row]).all())
+            continue
+        idx = np.nonzero(valid[:, p])[0]
+        n_p = int(ref["n"][p])
+        assert n_p == (idx < ref["n_hist"]).sum()
+        if rs is not None:
+            r_ref = vals[idx, p] - X[idx] @ ref["beta"][:, p]
+            assert np.isnan(np.delete(rs[row], idx)).all()
+            ymax = np.abs(vals[idx[:n_p], p]).max()
+            d = np.abs(rs[row, idx].astype(np.float64) - r_ref)
+            assert (d <= 1e-9 * ymax + EPS_OUT * np.abs(r_ref)).all(), (p, d.max())
+            worst_r = max(worst_r, d.max() / max(ymax, 1e-30))
+        mon = idx[n_p:]
+        assert np.isnan(np.delete(mo[row], mon)).all()
+        g = mo[row, mon].astype(np.float64)
+        if st == 3:
+            assert (g == 0).all()
+            continue
+        if st == 4:
+            assert mon.size == 0
+            continue
+        tr = ref["mo_trace"][p][: mon.size]
+        d = np.abs(g - tr)
+        assert (d <= 1e-9 * np.maximum(1.0, np.abs(tr)) + EPS_OUT * np.abs(tr)).all(), (p, d.max())
+        worst_mo = max(worst_mo, (d / np.maximum(1.0, np.abs(tr))).max())
+        # the trace crosses the boundary first where bfm_monitor/the oracle put the break
+        if ref["margin"][p] > 1e-5:
+            j = np.arange(n_p + 1, n_p + 1 + mon.size)
+            b = np.array([oracle.boundary(lam, int(jj), n_p) for jj in j])
+            cross = np.nonzero(np.abs(g) > b)[0]
+            first = mon[cross[0]] if cross.size else -1
+            assert first == ref["break_idx"][p], (p, first, ref["break_idx"][p])
+            checked_breaks += 1
+    return worst_mo, worst_r, checked_breaks

@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import synth
-from _parity import compare, to_numpy
+from _parity import check_trace_rows, compare, to_numpy
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -183,6 +183,16 @@ def c2_full(bfm):
         torch.cuda.synchronize()
         assert bfm.bfm_device_errors() == 0
         res[algo] = to_numpy(out)
+        if algo == 2:
+            # bfm_trace of sampled pixels while the scene is resident (offsets t*m + p beyond 2^31)
+            rng = np.random.default_rng(5)
+            brk = np.nonzero(res[2]["break_idx"] >= 0)[0]
+            sel = np.unique(np.concatenate([[0, w["m"] - 1], rng.choice(brk, 256, replace=False),
+                                            rng.choice(w["m"], 256, replace=False)])).astype(np.int64)
+            tr = bfm.trace(d, Yd, n_hist=w["n_hist"], h_frac=w["h_frac"], status=out["status"],
+                           pixels=torch.from_numpy(sel).cuda())
+            torch.cuda.synchronize()
+            res["trace"] = (sel, tr["mo"].cpu().numpy(), tr["resid"].cpu().numpy())
         del out
     del Yd
     torch.cuda.empty_cache()
@@ -202,6 +212,23 @@ def test_c2_full_scene_sampled(c2_full, algo):
     gpu = {k: (v[:, idx] if v.ndim == 2 else v[idx]) for k, v in res.items()}
     ws = dict(w, m=idx.size)
     _check(ws, Ys, gpu)
+
+
+def test_c2_full_scene_trace(c2_full):
+    """bfm_trace on the full-size scene: residuals and MO process of 514
+    sampled pixels (half of them with a break) against the oracle run on
+    those pixels' columns."""
+    w, res = c2_full
+    sel, mo, rs = res["trace"]
+    Ys = np.ascontiguousarray(w["Y"][:, sel])
+    ref = oracle.monitor(w["dates"], Ys, k=3, f=23.0, n_hist=w["n_hist"], h_frac=w["h_frac"], lam=w["lam"],
+                         trace=True)
+    ref["n_hist"] = w["n_hist"]
+    vals, valid = oracle.valid_and_values(Ys)
+    X = oracle.design(w["dates"], 3, 23.0)
+    wm, wr, nb = check_trace_rows(np.arange(sel.size), mo, rs, ref, vals, valid, X, w["lam"], m=sel.size)
+    print("worst MO error", wm, "worst residual error / max|y|", wr, "breaks checked", nb)
+    assert nb > 100
 
 
 @ALGOS
