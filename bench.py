@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 METRIC = "BFAST-monitor pixels/s at 8.4M px x 414 dates; p50/p99 tile latency"
 # DRAM bytes per pixel per launch from the ncu captures summarised in
 # profiles/ (None once the kernel changes after the capture).
-TRAFFIC_PER_PX = {"f32": (1.7866e9 / 1048576,), "f32simt": (None,), "i16": (None,)}
+TRAFFIC_PER_PX = {"f32": (1.7866e9 / 1048576,), "f32simt": (None,), "i16": (None,), "f32complete": (None,)}
 
 WORKLOAD = "c2: full scene 8,388,608 px x 414 dates, n_hist=228, K=8, f=23, h=0.25, plain float32"
 
@@ -280,6 +280,10 @@ def run_ours(args):
         if form in ("f32", "f32simt"):
             Yf, dt = Y, bfm.BFM_F32
             algo = bfm.BFM_ALGO_MMA if form == "f32" else bfm.BFM_ALGO_SIMT
+        elif form == "f32complete":
+            # the same scene recipe without clouds: the shared pseudo-inverse form
+            Yf = synth.workload_torch("c2_complete", device=dev, dtype="f32", m=args.pixels)["Y"]
+            dt, algo = bfm.BFM_F32, bfm.BFM_ALGO_COMPLETE
         else:
             Yf = torch.where(torch.isnan(Y), torch.full_like(Y, -32768.0),
                              torch.clamp(torch.round(Y * 1e4), -32767, 32767)).to(torch.int16)
@@ -329,7 +333,8 @@ def run_ours(args):
                              TRAFFIC_PER_PX[form][0] * m, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                              "algorithmic_bytes_per_launch": alg_bytes},
                 "clocks": clk, "dtype": "i16" if form == "i16" else "f32",
-                "algo": "simt" if form == "f32simt" else "tcgen05"}
+                "algo": {"f32simt": "simt", "f32complete": "complete-series (shared pseudo-inverse)"}.get(form,
+                                                                                                       "tcgen05")}
 
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
     res = {f: time_form(f) for f in forms}
@@ -427,9 +432,10 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--forms", default="f32,f32simt,i16",
+    ap.add_argument("--forms", default="f32,f32simt,i16,f32complete",
                     help="comma list; the first is the headline (f32 = float storage on tensor cores, "
-                         "f32simt = float storage on CUDA cores, i16 = int16 storage on tensor cores)")
+                         "f32simt = float storage on CUDA cores, i16 = int16 storage on tensor cores, "
+                         "f32complete = the same scene without clouds in the shared pseudo-inverse form)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-c4c5", action="store_true", help="skip the uneven-tile batch and serving legs")
     ap.add_argument("--pixels", type=int, default=None,

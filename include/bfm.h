@@ -60,6 +60,7 @@ enum {
     BFM_PX_SINGULAR = 2,             /* rank test failed (see bfm_monitor); NaN outputs */
     BFM_PX_DEGENERATE = 3,           /* sigma-hat <= 1e-6 max|y_hist|: MO = 0, mean 0 */
     BFM_PX_NO_MONITOR = 4,           /* no valid monitoring observation: mean NaN */
+    BFM_PX_INCOMPLETE = 5,           /* BFM_ALGO_COMPLETE only: a missing value; NaN outputs */
     BFM_PX_TIMEOUT = 255             /* the tile's load wait gave up (device error) */
 };
 
@@ -68,11 +69,26 @@ enum {
  * the N dates, a MOSUM ring of floor(h_frac * n_hist) + 17 prefix sums per
  * pixel, the Y stages) fits one SM, and Y can be described by a tensor map
  * (16-byte aligned base, m >= 128, rows a multiple of 16 bytes) -- else the
- * CUDA-core form (bfm_algo_auto tells which). */
+ * CUDA-core form (bfm_algo_auto tells which).
+ * BFM_ALGO_COMPLETE is never chosen by AUTO: it is the fast path for series
+ * without missing values (Section 3, Eq. 8-11), where every pixel shares the
+ * history design X_h and beta = M y_h with one M = (X_h'X_h)^-1 X_h' built in
+ * FP64 on the host on first use per (design, n_hist) (a synchronous upload
+ * of (n_hist + N) * K floats, kept with the design).  One thread per pixel
+ * streams its column: beta = M y_h (FP32, 32-date blocks added with TwoSum
+ * compensation), the history residuals and sigma-hat (history re-read from
+ * L2), then the monitoring dates with a running window sum whose leaving
+ * term is recomputed from y (Algorithm 3).  The same outputs as the other
+ * forms, with h = clamp(floor(h_frac * n_hist), 1, n_hist) for every pixel;
+ * when the shared design fails the rank test every pixel is SINGULAR
+ * (n_hist <= K: INSUFFICIENT_HISTORY).  A pixel with any missing value
+ * (NaN, -32768 or a 0 mask bit) gets BFM_PX_INCOMPLETE, break -1 and NaN
+ * outputs; run the general forms on such pixels. */
 typedef enum {
     BFM_ALGO_AUTO = 0,
     BFM_ALGO_SIMT = 1, /* FP32 CUDA-core path ("plain form") */
-    BFM_ALGO_MMA = 2   /* tensor-core normal equations, fitted values and refinement */
+    BFM_ALGO_MMA = 2,  /* tensor-core normal equations, fitted values and refinement */
+    BFM_ALGO_COMPLETE = 3 /* series without missing values: one shared pseudo-inverse */
 } bfm_algo;
 
 typedef struct bfm_design_s *bfm_design_t;

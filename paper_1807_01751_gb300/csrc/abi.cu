@@ -303,6 +303,7 @@ bfm_status bfm_design_destroy(bfm_design_t d) {
                 cudaFree(d->d_basis);
                 if (d->d_phi_tc) cudaFree(d->d_phi_tc);
                 if (d->d_dates) cudaFree(d->d_dates);
+                for (auto& c : d->complete) cudaFree(c.d_tab);
                 if (cur != d->device) cudaSetDevice(cur);
                 delete d;
             }
@@ -341,10 +342,13 @@ bfm_status bfm_monitor_ext(bfm_design_t d, const void* Y, int dtype, const uint3
         set_error("bfm_monitor: the design belongs to another device");
         return BFM_EINVAL;
     }
-    if (algo != BFM_ALGO_AUTO && algo != BFM_ALGO_SIMT && algo != BFM_ALGO_MMA) {
+    if (algo != BFM_ALGO_AUTO && algo != BFM_ALGO_SIMT && algo != BFM_ALGO_MMA && algo != BFM_ALGO_COMPLETE) {
         set_error("bfm_monitor: unknown algo");
         return BFM_EINVAL;
     }
+    if (algo == BFM_ALGO_COMPLETE)
+        return launch_complete(d, dtype, Y, mask_bits, m, n_hist, h_frac, lambda, break_idx, mean_mosum, sigma, beta,
+                               status, (cudaStream_t)stream, max_mosum);
     const bool mma_ok = mma_supported(d, dtype, n_hist, h_frac, Y, m, nullptr);
     if (algo == BFM_ALGO_MMA && !mma_ok) {
         set_error("bfm_monitor: the tensor-core form needs basis tables and a MOSUM ring (bandwidth + 17 prefix sums per pixel) that fits shared memory, and Y with a 16-byte aligned base, m >= 128 and rows of a multiple of 16 bytes");
@@ -477,11 +481,12 @@ bfm_status bfm_device_errors(void* stream, uint32_t* bits) {
         set_error("bfm_device_errors: bits is NULL");
         return BFM_EINVAL;
     }
-    unsigned int v = 0, v2 = 0;
+    unsigned int v = 0, v2 = 0, v3 = 0;
     cudaError_t e = simt_read_clear_errors((cudaStream_t)stream, &v);
     if (e == cudaSuccess) e = mma_read_clear_errors((cudaStream_t)stream, &v2);
+    if (e == cudaSuccess) e = complete_read_clear_errors((cudaStream_t)stream, &v3);
     if (e != cudaSuccess) return cuda_fail(e, "bfm_device_errors");
-    v |= v2;
+    v |= v2 | v3;
     *bits = v;
     return BFM_OK;
 }

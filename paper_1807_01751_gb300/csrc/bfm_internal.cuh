@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -129,6 +130,15 @@ cudaError_t simt_read_clear_errors(cudaStream_t s, unsigned int* bits);
 // ---------------------------------------------------------------------------
 // Public design handle
 // ---------------------------------------------------------------------------
+// Shared table of the complete-series form for one history length
+// (complete.cu): M' [n_hist][K] then X [N][K] in float, and the status every
+// pixel gets from the shared design (OK, INSUFFICIENT_HISTORY or SINGULAR).
+struct CompleteTab {
+    int n_hist;
+    int status;
+    float* d_tab;
+};
+
 struct bfm_design_s {
     int N = 0, k = 0, K = 0;
     double f = 0.0;
@@ -137,6 +147,8 @@ struct bfm_design_s {
     int NB = 0;               // basis row stride (floats)
     float* d_basis = nullptr; // device [N][NB]
     double* d_dates = nullptr; // device [N]: the date values (bfm_trace)
+    std::mutex complete_mu;            // guards `complete`
+    std::vector<CompleteTab> complete; // built on first use per n_hist, freed with the design
     // Tensor-core B operands: the basis table as fp16 hi and lo parts in the
     // no-swizzle core-matrix layout (see abi.cu tc_tables); nullptr when N
     // exceeds the tensor-core limit.
@@ -167,6 +179,13 @@ bfm_status launch_mma(const bfm_design_s* d, int dtype, const void* Y, const uin
                       int n_hist, double h_frac, double lambda, int32_t* brk, float* mean, float* sigma,
                       float* beta, uint8_t* status, cudaStream_t stream, float* maxmo = nullptr);
 cudaError_t mma_read_clear_errors(cudaStream_t s, unsigned int* bits);
+
+// Complete-series form (complete.cu): shared pseudo-inverse, one thread per pixel.
+size_t complete_smem_bytes(int N, int n, int K, int h, bool staged);
+cudaError_t complete_read_clear_errors(cudaStream_t s, unsigned int* bits);
+bfm_status launch_complete(bfm_design_s* d, int dtype, const void* Y, const uint32_t* mask, int64_t m, int n_hist,
+                           double h_frac, double lambda, int32_t* brk, float* mean, float* sigma, float* beta,
+                           uint8_t* status, cudaStream_t stream, float* maxmo);
 
 // Shared-memory bytes the SIMT kernel needs for N dates, k harmonics and a dtype (0 if too large).
 size_t simt_smem_bytes(int N, int k, int dtype, int* box_rows, int* nbox);

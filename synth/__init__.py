@@ -129,6 +129,10 @@ WORKLOADS = {
     "c2": dict(seed=2, m=8388608, N=414, n_hist=228, f=23.0, k=3, h_frac=0.25, dtype="f32",
                gen=dict(k_gen=3, intercept=0.5, slope=0.0, coef_umax=0.3, noise_sd=0.04,
                         miss="markov", p_a=0.25, p_b=0.375, break_frac=0.1, step=(-0.5, -0.1))),
+    # the c2 scene without clouds (series with no missing value: the shared pseudo-inverse form)
+    "c2_complete": dict(seed=2, m=8388608, N=414, n_hist=228, f=23.0, k=3, h_frac=0.25, dtype="f32", lam_of="c2",
+                        gen=dict(k_gen=3, intercept=0.5, slope=0.0, coef_umax=0.3, noise_sd=0.04,
+                                 miss="none", break_frac=0.1, step=(-0.5, -0.1))),
     "c3": dict(seed=1, m=4096, N=228, n_hist=100, f=23.0, k=3, h_frac=0.25, dtype="i16",
                gen=dict(k_gen=2, intercept=0.5, slope=0.001, coef_fixed=[0.2, 0.0, 0.0, 0.05],
                         noise_sd=0.03, miss="iid", p_a=0.3, break_frac=0.2, step=(-0.3, -0.3))),
@@ -145,7 +149,7 @@ def workload(name: str, *, m: int | None = None, out_ptr: int | None = None, dty
     d, Y, brk = scene(seed=w["seed"], m=mm, N=w["N"], n_hist=w["n_hist"], f=w["f"], dtype=dt,
                       out_ptr=out_ptr, **w["gen"])
     return dict(name=name, dates=d, Y=Y, true_break=brk, m=mm, N=w["N"], n_hist=w["n_hist"],
-                f=w["f"], k=w["k"], h_frac=w["h_frac"], lam=workload_lambda(name), dtype=dt)
+                f=w["f"], k=w["k"], h_frac=w["h_frac"], lam=workload_lambda(w.get("lam_of", name)), dtype=dt)
 
 
 def tiles_c4(seed: int = 4, count: int = 64, scale: float = 1.0, px_multiple: int = 1):
@@ -252,7 +256,7 @@ def workload_torch(name: str, *, m: int | None = None, device="cuda", dtype: str
     d, Y, brk = scene_torch(seed=w["seed"], m=mm, N=w["N"], n_hist=w["n_hist"], f=w["f"], dtype=dt,
                             device=device, **w["gen"])
     return dict(name=name, dates=d, Y=Y, true_break=brk, m=mm, N=w["N"], n_hist=w["n_hist"], f=w["f"],
-                k=w["k"], h_frac=w["h_frac"], lam=workload_lambda(name), dtype=dt)
+                k=w["k"], h_frac=w["h_frac"], lam=workload_lambda(w.get("lam_of", name)), dtype=dt)
 
 
 def lambda_for_horizon(T: float) -> float:
