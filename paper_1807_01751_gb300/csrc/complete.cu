@@ -28,7 +28,10 @@
 // 1, n) for every pixel, and positions are date indices, so this is exactly
 // the general definition.  A pixel that meets a missing value anywhere gets
 // status BFM_PX_INCOMPLETE and NaN outputs (the general forms handle it).
+#include <cudaTypedefs.h>
+
 #include <cmath>
+#include <cstring>
 #include <mutex>
 #include <type_traits>
 #include <vector>
@@ -111,11 +114,13 @@ __device__ __forceinline__ int16_t ld_hint(const int16_t* p, uint64_t pol) {
     return (int16_t)q;
 }
 
-// Missing markers: NaN (float), -32768 (int16).
-__device__ __forceinline__ bool present(float v) { return !isnan(v); }
-__device__ __forceinline__ bool present(int16_t q) { return q != (int16_t)-32768; }
-__device__ __forceinline__ float value(float v) { return v; }
-__device__ __forceinline__ float value(int16_t q) { return (float)q; }
+// The value of an observation, NaN when it is missing (float: NaN already;
+// int16: -32768).  A missing value then poisons beta0 (history) or the window
+// sum (monitoring), and a pixel is complete exactly when neither is NaN.
+__device__ __forceinline__ float obs_value(float v) { return v; }
+__device__ __forceinline__ float obs_value(int16_t q) {
+    return q == (int16_t)-32768 ? __int_as_float(0x7fc00000) : (float)q;
+}
 
 // Error-free sum: hi + lo gains x exactly (TwoSum), lo collects the errors.
 __device__ __forceinline__ void comp_add(float& hi, float& lo, float x) {
@@ -143,19 +148,21 @@ __device__ __forceinline__ float residual2(float y, const float* x, const float 
 
 // Shared-memory layout of one CTA: M' [n][K], X [N][K], the squared boundary
 // [N - n] and the window sums of the regressors [K] (floats); then, in the
-// staged form, 16-byte aligned: the last h residuals of each thread
+// staged form, 128-byte aligned: the last h residuals of each thread
 // [h][kThreads] floats, kStages stages of kStageBytes of Y, the stages' full
 // and empty mbarriers, and an abort flag.
 __host__ __device__ inline size_t ring_offset(int N, int n, int K) {
-    return ((size_t)(n + N) * K + (size_t)(N - n) + (size_t)K + 3) & ~(size_t)3;
+    return ((size_t)(n + N) * K + (size_t)(N - n) + (size_t)K + 31) & ~(size_t)31;  // 128-byte aligned
 }
 
-// 1-D bulk copy global -> shared completing on `bar`, with an L2 policy.
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t pol) {
+// 2-D tiled TMA load of the box at (x = pixel, y = date) completing on `bar`,
+// with an L2 policy.
+__device__ __forceinline__ void tma_load_2d_hint(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                                 uint64_t pol) {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::
-            "r"(ptx::smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(ptx::smem_u32(bar)), "l"(pol)
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(ptx::smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(ptx::smem_u32(bar)), "l"(pol)
         : "memory");
 }
 
@@ -172,7 +179,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // in shared memory.  Otherwise each thread loads its own values in register
 // batches and recomputes the leaving residual from y_{t-h}.
 template <int KH, typename T, bool kMask, bool kStaged>
-__global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2) complete_kernel(const CompleteParams P) {
+__global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2)
+    complete_kernel(const __grid_constant__ CUtensorMap tmap, const CompleteParams P) {
     constexpr int K = 2 + 2 * KH;
     constexpr int G1 = kStaged ? kStageBytes / (kThreads * (int)sizeof(T)) : kU1;  // dates per batch, history
     constexpr int G3 = kStaged ? G1 : kU3;                                          // dates per batch, monitoring
@@ -238,35 +246,22 @@ __global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2) complet
     const int64_t total = my_tiles * Q;
     int64_t j = 0;
     bool bad = false;
-    auto issue = [&](int64_t js) {  // thread 0: fill the slot of stage js
-        if (js >= total) return;
+    auto issue = [&](int64_t js) {  // producer: fill the slot of stage js with one box (256 pixels x G dates)
         const int64_t tl = js / Q;
         const int k = (int)(js - tl * Q);
-        const int64_t px0 = (blockIdx.x + tl * gridDim.x) * kThreads;
-        const int64_t rem = m - px0;
-        const uint32_t rowb = (uint32_t)((rem < kThreads ? rem : kThreads) * (int64_t)sizeof(T));
-        int d0, cnt;
-        if (k < 2 * ng1) {
-            d0 = (k < ng1 ? k : k - ng1) * G1;
-            cnt = min(G1, n - d0);
-        } else {
-            d0 = n + (k - 2 * ng1) * G3;
-            cnt = min(G3, N - d0);
-        }
+        const int px0 = (int)((blockIdx.x + tl * gridDim.x) * kThreads);
+        const int d0 = k < 2 * ng1 ? (k < ng1 ? k : k - ng1) * G1 : n + (k - 2 * ng1) * G3;
         const int slot = (int)(js % kStages);
-        uint64_t* bar = full + slot;
-        ptx::mbar_arrive_expect_tx(bar, (uint32_t)cnt * rowb);
-        unsigned char* dst = stages + slot * kStageBytes;
-        const T* src = static_cast<const T*>(P.Y) + (size_t)d0 * (size_t)m + px0;
-        for (int r = 0; r < cnt; ++r) {
-            // pass 1 keeps the history in L2 for pass 2; pass 2 keeps the dates
-            // the first windows re-read (ring form: none) and drops the rest
-            const uint64_t pol = k < ng1 ? keep : (k < 2 * ng1 ? drop : normal);
-            bulk_load(dst + (size_t)r * kThreads * sizeof(T), src + (size_t)r * (size_t)m, rowb, bar, pol);
-        }
+        // pass 1 keeps the history in L2 for pass 2, pass 2 drops it (the
+        // ring holds the residuals the first windows need)
+        const uint64_t pol = k < ng1 ? keep : (k < 2 * ng1 ? drop : normal);
+        // pixels past m and dates past N arrive as zeros; the box is always full
+        ptx::mbar_arrive_expect_tx(full + slot, (uint32_t)kStageBytes);
+        tma_load_2d_hint(stages + slot * kStageBytes, &tmap, full + slot, px0, d0, pol);
     };
     if (kStaged && threadIdx.x >= kThreads) {  // the producer warp: one lane issues
         if (threadIdx.x == kThreads) {
+            ptx::prefetch_tmap(&tmap);
             int64_t js = 0;
             for (; js < total; ++js) {
                 const int slot = (int)(js % kStages);
@@ -315,7 +310,6 @@ __global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2) complet
 #pragma unroll
         for (int a = 0; a < K; ++a) b0[a] = 0.f;
         float ymax = 0.f;
-        bool complete = true;
         auto pass1 = [&](int d0, auto full_c) {
             constexpr bool full = decltype(full_c)::value;
             const int cnt = full ? G1 : n - d0;
@@ -343,9 +337,9 @@ __global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2) complet
             }
 #pragma unroll
             for (int u = 0; u < G1; ++u) {
-                const bool ok = present(raw[u]) && (!kMask || (mw[u] & mbit));
-                complete = complete && ok;
-                const float v = ok ? value(raw[u]) : 0.f;
+                // past the end of a partial batch raw = 0 and the mask word is all ones
+                float v = obs_value(raw[u]);
+                if (kMask && !(mw[u] & mbit)) v = __int_as_float(0x7fc00000);
                 ymax = fmaxf(ymax, fabsf(v));
                 const float* mt = sM + (full ? d0 + u : min(d0 + u, n - 1)) * K;
 #pragma unroll
@@ -364,8 +358,9 @@ __global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2) complet
         // differs from sum r^2 by a second-order term); the first window's
         // h - 1 oldest residuals (kept in the ring in the staged form).
         float c0 = 0.f, c1 = 0.f, ss = 0.f, W0 = 0.f;
-        auto pass2 = [&](int d0, auto full_c) {
+        auto pass2 = [&](int d0, auto full_c, auto win_c) {
             constexpr bool full = decltype(full_c)::value;
+            constexpr bool win = decltype(win_c)::value;  // the batch may reach the first window (t >= w0)
             const int cnt = full ? G1 : n - d0;
             T raw[G1];
             if constexpr (kStaged) {
@@ -383,20 +378,25 @@ __global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2) complet
 #pragma unroll
             for (int u = 0; u < G1; ++u) {
                 const int t = d0 + u, tc = full ? t : min(t, n - 1);
-                float r = residual<K>(value(raw[u]), sX + tc * K, b0);
+                float r = residual<K>(obs_value(raw[u]), sX + tc * K, b0);
                 if (!full) r = u < cnt ? r : 0.f;
                 ss = fmaf(r, r, ss);
                 c0 = fmaf(sM[tc * K], r, c0);
                 c1 = fmaf(sM[tc * K + 1], r, c1);
-                if (t >= w0 && (full || u < cnt)) {
+                if (win && t >= w0 && (full || u < cnt)) {
                     W0 += r;
                     if (kStaged) ring[(t - w0) * kThreads] = r;
                 }
             }
             if constexpr (kStaged) release();
         };
-        for (d0 = 0; d0 + G1 <= n && !bad; d0 += G1) pass2(d0, std::true_type{});
-        if (d0 < n && !bad) pass2(d0, std::false_type{});
+        for (d0 = 0; d0 + G1 <= n && !bad; d0 += G1) {
+            if (d0 + G1 <= w0)
+                pass2(d0, std::true_type{}, std::false_type{});
+            else
+                pass2(d0, std::true_type{}, std::true_type{});
+        }
+        if (d0 < n && !bad) pass2(d0, std::false_type{}, std::true_type{});
         // residuals from here on: beta0 with the intercept and trend corrected
         // by (c0, c1), kept apart (a float rounding of those two would enter
         // all h residuals of a window alike)
@@ -406,6 +406,7 @@ __global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2) complet
         const float sig = sqrtf(ss / (float)(n - K));
         const bool degenerate = !(sig > 1e-6f * ymax) || ymax == 0.f;
         const float inv_scale = degenerate ? 0.f : 1.f / (sig * sqrtf((float)n));
+        const float inv2 = inv_scale * inv_scale;
 
         // pass 3: monitoring dates.  The residual leaving the window is the
         // ring slot of date t - h (the same slot as date t), or, in the plain
@@ -440,29 +441,37 @@ __global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2) complet
                     qm += mws;
                 }
             }
-            float blk = 0.f;
+            // boundary test MO^2 > b^2 as W^2 inv_scale^2 - b^2 > 0: its maximum over
+            // the batch, and the first crossing searched only in a batch that has one
+            float blk = 0.f, cmax = -INFINITY, wv[G3];
 #pragma unroll
             for (int u = 0; u < G3; ++u) {
                 const int t = d0 + u;
+                wv[u] = 0.f;
                 if (full || u < cnt) {
-                    const bool ok = present(raw[u]) && (!kMask || (mw[u] & mbit));
-                    complete = complete && ok;
-                    const float r = residual2<K>(value(raw[u]), sX + t * K, b0, c0, c1);
+                    float v = obs_value(raw[u]);
+                    if (kMask && !(mw[u] & mbit)) v = __int_as_float(0x7fc00000);
+                    const float r = residual2<K>(v, sX + t * K, b0, c0, c1);
                     float ro;
                     if constexpr (kStaged) {
                         ro = t > n ? ring[slot * kThreads] : 0.f;
                         ring[slot * kThreads] = r;
                         slot = slot + 1 == h ? 0 : slot + 1;
                     } else {
-                        ro = t > n ? residual2<K>(value(old[u]), sX + (t - h) * K, b0, c0, c1) : 0.f;
+                        ro = t > n ? residual2<K>(obs_value(old[u]), sX + (t - h) * K, b0, c0, c1) : 0.f;
                     }
                     W = (W + r) - ro;
-                    const float mo = W * inv_scale;
-                    if (brk < 0 && mo * mo > sB[t - n]) brk = t;
+                    wv[u] = W;
+                    cmax = fmaxf(cmax, fmaf(W * W, inv2, -sB[t - n]));
                     blk += W;
                     wmax = fmaxf(wmax, W);
                     wmin = fminf(wmin, W);
                 }
+            }
+            if (brk < 0 && cmax > 0.f) {
+#pragma unroll
+                for (int u = 0; u < G3; ++u)
+                    if ((full || u < cnt) && brk < 0 && fmaf(wv[u] * wv[u], inv2, -sB[d0 + u - n]) > 0.f) brk = d0 + u;
             }
             comp_add(sh, sl, blk);
             if constexpr (kStaged) release();
@@ -472,7 +481,7 @@ __global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2) complet
         if (bad) break;
         if (!active) continue;
 
-        if (!complete) {
+        if (isnan(b0[0]) || isnan(sh)) {  // a missing value met in the history or the monitoring period
             write_unfitted(p, BFM_PX_INCOMPLETE);
             continue;
         }
@@ -505,25 +514,40 @@ __global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2) complet
 }
 
 template <int KH, typename T, bool kMask, bool kStaged>
-bfm_status launch_variant(const CompleteParams& P, int grid, size_t smem, cudaStream_t st) {
+bfm_status launch_variant(const CUtensorMap& tm, const CompleteParams& P, int grid, size_t smem, cudaStream_t st) {
     auto* fn = complete_kernel<KH, T, kMask, kStaged>;
     if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_fail(e, "bfm_monitor (complete): shared memory attribute");
     }
-    fn<<<grid, kStaged ? kThreads + 32 : kThreads, smem, st>>>(P);
+    fn<<<grid, kStaged ? kThreads + 32 : kThreads, smem, st>>>(tm, P);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "bfm_monitor (complete): launch");
     return BFM_OK;
 }
 
 template <int KH, bool kStaged>
-bfm_status launch_kh(const CompleteParams& P, int dtype, int grid, size_t smem, cudaStream_t st) {
+bfm_status launch_kh(const CUtensorMap& tm, const CompleteParams& P, int dtype, int grid, size_t smem,
+                     cudaStream_t st) {
     if (dtype == BFM_F32)
-        return P.mask ? launch_variant<KH, float, true, kStaged>(P, grid, smem, st)
-                      : launch_variant<KH, float, false, kStaged>(P, grid, smem, st);
-    return P.mask ? launch_variant<KH, int16_t, true, kStaged>(P, grid, smem, st)
-                  : launch_variant<KH, int16_t, false, kStaged>(P, grid, smem, st);
+        return P.mask ? launch_variant<KH, float, true, kStaged>(tm, P, grid, smem, st)
+                      : launch_variant<KH, float, false, kStaged>(tm, P, grid, smem, st);
+    return P.mask ? launch_variant<KH, int16_t, true, kStaged>(tm, P, grid, smem, st)
+                  : launch_variant<KH, int16_t, false, kStaged>(tm, P, grid, smem, st);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    });
+    return fn;
 }
 
 // The shared table of (design, n_hist): M' and X in float, built in FP64.
@@ -609,8 +633,8 @@ bfm_status complete_table(bfm_design_s* d, int n, const float** tab, int* status
 
 }  // namespace
 
-// Shared memory of the complete-series kernel (staged form: ring, stages and
-// their barriers on top of the tables).
+// Shared memory of the complete-series kernel (staged form: ring, stages,
+// their barriers and the abort flag on top of the tables).
 size_t complete_smem_bytes(int N, int n, int K, int h, bool staged) {
     return sizeof(float) * ring_offset(N, n, K) +
            (staged ? sizeof(float) * (size_t)h * kThreads + (size_t)kStages * (kStageBytes + 16) + 16 : 0);
@@ -655,16 +679,29 @@ bfm_status launch_complete(bfm_design_s* d, int dtype, const void* Y, const uint
     // staged form: bulk copies need 16-byte aligned rows (base and m * elt), and
     // the ring, stages and tables must leave room for two CTAs per SM
     const bool aligned = ((uintptr_t)Y % 16 == 0) && ((size_t)m * elt % 16 == 0);
-    const bool staged = aligned && complete_smem_bytes(d->N, n_hist, d->K, P.h, true) <= kSmemMax;
+    bool staged = aligned && complete_smem_bytes(d->N, n_hist, d->K, P.h, true) <= kSmemMax;
+    CUtensorMap tm;
+    std::memset(&tm, 0, sizeof tm);
+    if (staged) {  // Y as a 2-D tensor (pixels innermost), boxes of 256 pixels x one stage of dates
+        auto enc = encode_fn();
+        const cuuint64_t gdim[2] = {(cuuint64_t)m, (cuuint64_t)d->N};
+        const cuuint64_t gstride[1] = {(cuuint64_t)m * elt};
+        const cuuint32_t box[2] = {(cuuint32_t)kThreads, (cuuint32_t)(kStageBytes / (kThreads * elt))};
+        const cuuint32_t es[2] = {1u, 1u};
+        staged = enc && enc(&tm, elt == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 2,
+                            const_cast<void*>(Y), gdim, gstride, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    }
     const size_t smem = complete_smem_bytes(d->N, n_hist, d->K, P.h, staged);
     if (staged) {
-        if (d->k == 1) return launch_kh<1, true>(P, dtype, grid, smem, stream);
-        if (d->k == 2) return launch_kh<2, true>(P, dtype, grid, smem, stream);
-        return launch_kh<3, true>(P, dtype, grid, smem, stream);
+        if (d->k == 1) return launch_kh<1, true>(tm, P, dtype, grid, smem, stream);
+        if (d->k == 2) return launch_kh<2, true>(tm, P, dtype, grid, smem, stream);
+        return launch_kh<3, true>(tm, P, dtype, grid, smem, stream);
     }
-    if (d->k == 1) return launch_kh<1, false>(P, dtype, grid, smem, stream);
-    if (d->k == 2) return launch_kh<2, false>(P, dtype, grid, smem, stream);
-    return launch_kh<3, false>(P, dtype, grid, smem, stream);
+    if (d->k == 1) return launch_kh<1, false>(tm, P, dtype, grid, smem, stream);
+    if (d->k == 2) return launch_kh<2, false>(tm, P, dtype, grid, smem, stream);
+    return launch_kh<3, false>(tm, P, dtype, grid, smem, stream);
 }
 
 }  // namespace bfm
