@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 METRIC = "BFAST-monitor pixels/s at 8.4M px x 414 dates; p50/p99 tile latency"
 # DRAM bytes per pixel per launch from the ncu captures summarised in
 # profiles/ (None once the kernel changes after the capture).
-TRAFFIC_PER_PX = {"f32": (1.7866e9 / 1048576,), "f32simt": (None,), "i16": (None,), "f32complete": (None,)}
+TRAFFIC_PER_PX = {"f32": (1.7866e9 / 1048576,), "f32simt": (None,), "i16": (None,), "f32complete": (1.797e9 / 1048576,)}
 
 WORKLOAD = "c2: full scene 8,388,608 px x 414 dates, n_hist=228, K=8, f=23, h=0.25, plain float32"
 
