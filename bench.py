@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 METRIC = "BFAST-monitor pixels/s at 8.4M px x 414 dates; p50/p99 tile latency"
 # DRAM bytes per pixel per launch from the ncu captures summarised in
 # profiles/ (None once the kernel changes after the capture).
-TRAFFIC_PER_PX = {"f32": (1.7866e9 / 1048576,), "f32simt": (None,), "i16": (None,), "f32complete": (1.797e9 / 1048576,)}
+TRAFFIC_PER_PX = {"f32": (1.7866e9 / 1048576,), "f32simt": (None,), "f32stream": (None,), "i16": (None,), "f32complete": (1.797e9 / 1048576,)}
 
 WORKLOAD = "c2: full scene 8,388,608 px x 414 dates, n_hist=228, K=8, f=23, h=0.25, plain float32"
 
@@ -277,9 +277,9 @@ def run_ours(args):
     def time_form(form):
         """Device-resident timing of one form: W warm-up calls, then K calls
         bracketed by CUDA events on the launching stream."""
-        if form in ("f32", "f32simt"):
+        if form in ("f32", "f32simt", "f32stream"):
             Yf, dt = Y, bfm.BFM_F32
-            algo = bfm.BFM_ALGO_MMA if form == "f32" else bfm.BFM_ALGO_SIMT
+            algo = {"f32": bfm.BFM_ALGO_MMA, "f32simt": bfm.BFM_ALGO_SIMT, "f32stream": bfm.BFM_ALGO_STREAM}[form]
         elif form == "f32complete":
             # the same scene recipe without clouds: the shared pseudo-inverse form
             Yf = synth.workload_torch("c2_complete", device=dev, dtype="f32", m=args.pixels)["Y"]
@@ -333,8 +333,8 @@ def run_ours(args):
                              TRAFFIC_PER_PX[form][0] * m, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                              "algorithmic_bytes_per_launch": alg_bytes},
                 "clocks": clk, "dtype": "i16" if form == "i16" else "f32",
-                "algo": {"f32simt": "simt", "f32complete": "complete-series (shared pseudo-inverse)"}.get(form,
-                                                                                                       "tcgen05")}
+                "algo": {"f32simt": "simt", "f32stream": "stream (CUDA cores, TMA stages)",
+                         "f32complete": "complete-series (shared pseudo-inverse)"}.get(form, "tcgen05")}
 
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
     res = {f: time_form(f) for f in forms}
@@ -432,8 +432,9 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--forms", default="f32,f32simt,i16,f32complete",
+    ap.add_argument("--forms", default="f32,f32stream,f32simt,i16,f32complete",
                     help="comma list; the first is the headline (f32 = float storage on tensor cores, "
+                         "f32stream = float storage, one CUDA-core thread per pixel streamed through TMA stages, "
                          "f32simt = float storage on CUDA cores, i16 = int16 storage on tensor cores, "
                          "f32complete = the same scene without clouds in the shared pseudo-inverse form)")
     ap.add_argument("--no-e2e", action="store_true")

@@ -83,12 +83,23 @@ enum {
  * when the shared design fails the rank test every pixel is SINGULAR
  * (n_hist <= K: INSUFFICIENT_HISTORY).  A pixel with any missing value
  * (NaN, -32768 or a 0 mask bit) gets BFM_PX_INCOMPLETE, break -1 and NaN
- * outputs; run the general forms on such pixels. */
+ * outputs; run the general forms on such pixels.
+ * BFM_ALGO_STREAM: the general definition (missing values allowed) with one
+ * CUDA-core thread per pixel.  Each pixel's column is streamed four times
+ * (masked basis sums and X'My; refinement sums; the first window; the
+ * monitoring dates) through shared-memory stages filled by 2-D TMA boxes of
+ * 256 pixels, the history kept in L2 between its passes; FP32 normal
+ * equations with one refinement step as in the CUDA-core form, the MOSUM
+ * window from a per-thread ring of the last h_p residuals.  Needs Y with a
+ * 16-byte aligned base and rows of a multiple of 16 bytes, and the basis
+ * tables plus floor(h_frac * n_hist) ring slots per pixel within 112 KB of
+ * shared memory (else BFM_EUNSUPPORTED). */
 typedef enum {
     BFM_ALGO_AUTO = 0,
     BFM_ALGO_SIMT = 1, /* FP32 CUDA-core path ("plain form") */
     BFM_ALGO_MMA = 2,  /* tensor-core normal equations, fitted values and refinement */
-    BFM_ALGO_COMPLETE = 3 /* series without missing values: one shared pseudo-inverse */
+    BFM_ALGO_COMPLETE = 3, /* series without missing values: one shared pseudo-inverse */
+    BFM_ALGO_STREAM = 4    /* one CUDA-core thread per pixel, Y streamed through TMA stages */
 } bfm_algo;
 
 typedef struct bfm_design_s *bfm_design_t;

@@ -342,10 +342,14 @@ bfm_status bfm_monitor_ext(bfm_design_t d, const void* Y, int dtype, const uint3
         set_error("bfm_monitor: the design belongs to another device");
         return BFM_EINVAL;
     }
-    if (algo != BFM_ALGO_AUTO && algo != BFM_ALGO_SIMT && algo != BFM_ALGO_MMA && algo != BFM_ALGO_COMPLETE) {
+    if (algo != BFM_ALGO_AUTO && algo != BFM_ALGO_SIMT && algo != BFM_ALGO_MMA && algo != BFM_ALGO_COMPLETE &&
+        algo != BFM_ALGO_STREAM) {
         set_error("bfm_monitor: unknown algo");
         return BFM_EINVAL;
     }
+    if (algo == BFM_ALGO_STREAM)
+        return launch_stream(d, dtype, Y, mask_bits, m, n_hist, h_frac, lambda, break_idx, mean_mosum, sigma, beta,
+                             status, (cudaStream_t)stream, max_mosum);
     if (algo == BFM_ALGO_COMPLETE)
         return launch_complete(d, dtype, Y, mask_bits, m, n_hist, h_frac, lambda, break_idx, mean_mosum, sigma, beta,
                                status, (cudaStream_t)stream, max_mosum);
@@ -481,12 +485,13 @@ bfm_status bfm_device_errors(void* stream, uint32_t* bits) {
         set_error("bfm_device_errors: bits is NULL");
         return BFM_EINVAL;
     }
-    unsigned int v = 0, v2 = 0, v3 = 0;
+    unsigned int v = 0, v2 = 0, v3 = 0, v4 = 0;
     cudaError_t e = simt_read_clear_errors((cudaStream_t)stream, &v);
     if (e == cudaSuccess) e = mma_read_clear_errors((cudaStream_t)stream, &v2);
     if (e == cudaSuccess) e = complete_read_clear_errors((cudaStream_t)stream, &v3);
+    if (e == cudaSuccess) e = stream_read_clear_errors((cudaStream_t)stream, &v4);
     if (e != cudaSuccess) return cuda_fail(e, "bfm_device_errors");
-    v |= v2 | v3;
+    v |= v2 | v3 | v4;
     *bits = v;
     return BFM_OK;
 }

@@ -183,6 +183,13 @@ cudaError_t mma_read_clear_errors(cudaStream_t s, unsigned int* bits);
 // Complete-series form (complete.cu): shared pseudo-inverse, one thread per pixel.
 size_t complete_smem_bytes(int N, int n, int K, int h, bool staged);
 cudaError_t complete_read_clear_errors(cudaStream_t s, unsigned int* bits);
+
+// Streaming CUDA-core form (stream.cu).
+bool stream_supported(const bfm_design_s* d, int dtype, int n_hist, double h_frac, const void* Y, int64_t m);
+bfm_status launch_stream(const bfm_design_s* d, int dtype, const void* Y, const uint32_t* mask, int64_t m,
+                         int n_hist, double h_frac, double lambda, int32_t* brk, float* mean, float* sigma,
+                         float* beta, uint8_t* status, cudaStream_t stream, float* maxmo);
+cudaError_t stream_read_clear_errors(cudaStream_t s, unsigned int* bits);
 bfm_status launch_complete(bfm_design_s* d, int dtype, const void* Y, const uint32_t* mask, int64_t m, int n_hist,
                            double h_frac, double lambda, int32_t* brk, float* mean, float* sigma, float* beta,
                            uint8_t* status, cudaStream_t stream, float* maxmo);
