@@ -38,7 +38,9 @@ sys.path.insert(0, ROOT)
 METRIC = "BFAST-monitor pixels/s at 8.4M px x 414 dates; p50/p99 tile latency"
 # DRAM bytes per pixel per launch from the ncu captures summarised in
 # profiles/ (None once the kernel changes after the capture).
-TRAFFIC_PER_PX = {"f32": (1.7866e9 / 1048576,), "f32simt": (None,), "f32stream": (None,), "i16": (None,), "f32complete": (1.797e9 / 1048576,)}
+TRAFFIC_PER_PX = {"f32": (1.7866e9 / 1048576,), "f32simt": (None,), "f32stream": (1.8958e9 / 1048576,),
+                  "i16": (None,),
+                  "i16stream": (None,), "f32complete": (1.797e9 / 1048576,)}
 
 WORKLOAD = "c2: full scene 8,388,608 px x 414 dates, n_hist=228, K=8, f=23, h=0.25, plain float32"
 
@@ -178,7 +180,7 @@ def run_tiles_and_serving(bfm, synth, torch, dev, stream):
         design = bfm.Design(d, t["k"], 23.0)
         tiles.append(dict(t, Y=Y, design=design, lam=synth.lambda_for_horizon(t["N"] / t["n_hist"]),
                           out=bfm.empty_outputs(2 + 2 * t["k"], t["m"], dev),
-                          mma=bfm.bfm_algo_auto(design, bfm.BFM_I16, t["n_hist"], 0.25, Y, t["m"]) == bfm.BFM_ALGO_MMA))
+                          mma=bfm.bfm_batch_form(design, bfm.BFM_I16, t["n_hist"], 0.25, Y, t["m"]) == bfm.BFM_ALGO_MMA))
     total_px = sum(t["m"] for t in tiles)
     torch.cuda.synchronize()
 
@@ -287,7 +289,7 @@ def run_ours(args):
         else:
             Yf = torch.where(torch.isnan(Y), torch.full_like(Y, -32768.0),
                              torch.clamp(torch.round(Y * 1e4), -32767, 32767)).to(torch.int16)
-            dt, algo = bfm.BFM_I16, bfm.BFM_ALGO_MMA
+            dt, algo = bfm.BFM_I16, (bfm.BFM_ALGO_STREAM if form == "i16stream" else bfm.BFM_ALGO_MMA)
 
         def step():
             bfm.bfm_monitor_ex(design, Yf, dt, None, m, n_hist, w["h_frac"], w["lam"], out["break_idx"],
@@ -319,7 +321,7 @@ def run_ours(args):
             t = torch.tensor([total_ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             total_ms = float(t.item())
-        elt = 2 if form == "i16" else 4
+        elt = 2 if form.startswith("i16") else 4
         alg_bytes = N * m * elt + m * (4 + 4 + 4 + 4 * K + 1)
         achieved = alg_bytes / (statistics.mean(per) / 1e3) / 1e9
         srt = sorted(per)
@@ -332,8 +334,9 @@ def run_ours(args):
                              "frac": achieved / hbm, "traffic": TRAFFIC_PER_PX.get(form, (None,))[0] and
                              TRAFFIC_PER_PX[form][0] * m, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                              "algorithmic_bytes_per_launch": alg_bytes},
-                "clocks": clk, "dtype": "i16" if form == "i16" else "f32",
+                "clocks": clk, "dtype": "i16" if form.startswith("i16") else "f32",
                 "algo": {"f32simt": "simt", "f32stream": "stream (CUDA cores, TMA stages)",
+                         "i16stream": "stream (CUDA cores, TMA stages)",
                          "f32complete": "complete-series (shared pseudo-inverse)"}.get(form, "tcgen05")}
 
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
@@ -341,7 +344,7 @@ def run_ours(args):
     form = forms[0]
     main = res[form]
     value, ms_step = main["value"], main["ms_per_step"]
-    elt = 2 if form == "i16" else 4
+    elt = 2 if form.startswith("i16") else 4
 
     # ---- end to end (float32 scene through bfm_monitor_host) through the host-buffer entry point ------------------------------
     e2e = None
@@ -432,9 +435,10 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--forms", default="f32,f32stream,f32simt,i16,f32complete",
-                    help="comma list; the first is the headline (f32 = float storage on tensor cores, "
-                         "f32stream = float storage, one CUDA-core thread per pixel streamed through TMA stages, "
+    ap.add_argument("--forms", default="f32stream,f32,f32simt,i16stream,i16,f32complete",
+                    help="comma list; the first is the headline (f32stream = float storage, one CUDA-core "
+                         "thread per pixel streamed through TMA stages (the form AUTO takes), f32 = float "
+                         "storage on tensor cores, i16stream = int16 storage in the streaming form, "
                          "f32simt = float storage on CUDA cores, i16 = int16 storage on tensor cores, "
                          "f32complete = the same scene without clouds in the shared pseudo-inverse form)")
     ap.add_argument("--no-e2e", action="store_true")

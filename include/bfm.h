@@ -65,6 +65,7 @@ enum {
 };
 
 /* Algorithm variants for bfm_monitor_ex.  BFM_ALGO_AUTO takes the
+ * streaming form (BFM_ALGO_STREAM, below) where it applies, else the
  * tensor-core form where it applies -- its shared memory (basis tables over
  * the N dates, a MOSUM ring of floor(h_frac * n_hist) + 17 prefix sums per
  * pixel, the Y stages) fits one SM, and Y can be described by a tensor map
@@ -283,12 +284,12 @@ bfm_status bfm_monitor_host(bfm_design_t d, const void *Y_host, int dtype, const
  * Batched persistent launch -- many scene tiles of uneven pixel counts,
  * series lengths (their own designs), harmonics and storage types processed
  * by one CUDA-graph replay of persistent kernels: one per tensor-core kernel
- * variant (k, storage, mask) for the tiles BFM_ALGO_AUTO gives the
- * tensor-core form (128-pixel blocks), and one CUDA-core kernel for the rest
- * (32-pixel blocks).  The paper processes one scene per call (Algorithm 2);
- * batching is a serving extension with the same per-pixel results: every
- * pixel's outputs equal those of bfm_monitor with BFM_ALGO_AUTO on its tile
- * alone.
+ * variant (k, storage, mask) for the tiles the tensor-core form takes
+ * (128-pixel blocks), and one CUDA-core kernel for the rest (32-pixel
+ * blocks); bfm_batch_form tells which.  The paper processes one scene per
+ * call (Algorithm 2); batching is a serving extension with the same
+ * per-pixel results: every pixel's outputs equal those of bfm_monitor_ex
+ * with the form bfm_batch_form names, on its tile alone.
  *   bfm_batch_create    new empty batch on the current device (owned by the
  *                       caller, freed by bfm_batch_destroy).
  *   bfm_batch_add       appends one tile; arguments and errors as
@@ -320,6 +321,9 @@ bfm_status bfm_batch_run(bfm_batch_t b, void *stream);
 bfm_status bfm_batch_autotune(bfm_batch_t b, void *stream, int *ctas_per_sm, int *grab, float *best_ms);
 bfm_status bfm_batch_set_config(bfm_batch_t b, int ctas_per_sm, int grab);
 int bfm_batch_tiles(bfm_batch_t b);
+/* The form a tile with these arguments takes in a batch: BFM_ALGO_MMA or
+ * BFM_ALGO_SIMT (no work, no device access). */
+int bfm_batch_form(bfm_design_t d, int dtype, int n_hist, double h_frac, const void *Y, int64_t m);
 bfm_status bfm_batch_destroy(bfm_batch_t b);
 
 /*

@@ -97,6 +97,8 @@ def load(build_if_missing: bool = True):
         lib.bfm_monitor_ext.restype = i32
         lib.bfm_algo_auto.argtypes = [vp, i32, i32, dbl, vp, i64]
         lib.bfm_algo_auto.restype = i32
+        lib.bfm_batch_form.argtypes = [vp, i32, i32, dbl, vp, i64]
+        lib.bfm_batch_form.restype = i32
         lib.bfm_lambda.argtypes = [dbl, dbl, dbl, i32, i32, ctypes.c_uint64, ctypes.POINTER(dbl), vp, vp]
         lib.bfm_lambda.restype = i32
         lib.bfm_trace.argtypes = [vp, vp, i32, vp, i64, i32, dbl, vp, i64, vp, vp, vp, vp]
@@ -231,6 +233,10 @@ def bfm_trace(design, Y, dtype, mask_bits, m, n_hist, h_frac, pixels, count, sta
 
 def bfm_algo_auto(design, dtype: int, n_hist: int, h_frac: float, Y, m: int) -> int:
     return load().bfm_algo_auto(int(design), int(dtype), int(n_hist), float(h_frac), _ptr(Y), int(m))
+
+
+def bfm_batch_form(design, dtype: int, n_hist: int, h_frac: float, Y, m: int) -> int:
+    return load().bfm_batch_form(int(design), int(dtype), int(n_hist), float(h_frac), _ptr(Y), int(m))
 
 
 def bfm_monitor_ext(design, Y, dtype, mask_bits, m, n_hist, h_frac, lam, break_idx, mean_mosum, sigma, beta,

@@ -184,6 +184,12 @@ bfm_status cuda_fail(cudaError_t e, const char* what) {
     return e == cudaErrorMemoryAllocation ? BFM_ENOMEM : BFM_ECUDA;
 }
 
+int auto_form(const bfm_design_s* d, int dtype, int n_hist, double h_frac, const void* Y, int64_t m) {
+    if (stream_supported(d, dtype, n_hist, h_frac, Y, m)) return BFM_ALGO_STREAM;
+    if (mma_supported(d, dtype, n_hist, h_frac, Y, m, nullptr)) return BFM_ALGO_MMA;
+    return BFM_ALGO_SIMT;
+}
+
 }  // namespace bfm
 
 using namespace bfm;
@@ -320,7 +326,7 @@ int bfm_design_N(bfm_design_t d) { return d ? d->N : 0; }
 
 int bfm_algo_auto(bfm_design_t d, int dtype, int n_hist, double h_frac, const void* Y, int64_t m) {
     if (!d || (dtype != BFM_F32 && dtype != BFM_I16) || !(n_hist >= 1 && n_hist < d->N)) return BFM_ALGO_SIMT;
-    return mma_supported(d, dtype, n_hist, h_frac, Y, m, nullptr) ? BFM_ALGO_MMA : BFM_ALGO_SIMT;
+    return auto_form(d, dtype, n_hist, h_frac, Y, m);
 }
 
 bfm_status bfm_monitor_ext(bfm_design_t d, const void* Y, int dtype, const uint32_t* mask_bits, int64_t m,
@@ -358,6 +364,9 @@ bfm_status bfm_monitor_ext(bfm_design_t d, const void* Y, int dtype, const uint3
         set_error("bfm_monitor: the tensor-core form needs basis tables and a MOSUM ring (bandwidth + 17 prefix sums per pixel) that fits shared memory, and Y with a 16-byte aligned base, m >= 128 and rows of a multiple of 16 bytes");
         return BFM_EUNSUPPORTED;
     }
+    if (algo == BFM_ALGO_AUTO && stream_supported(d, dtype, n_hist, h_frac, Y, m))
+        return launch_stream(d, dtype, Y, mask_bits, m, n_hist, h_frac, lambda, break_idx, mean_mosum, sigma, beta,
+                             status, (cudaStream_t)stream, max_mosum);
     if (algo == BFM_ALGO_MMA || (algo == BFM_ALGO_AUTO && mma_ok))
         return launch_mma(d, dtype, Y, mask_bits, m, n_hist, h_frac, lambda, break_idx, mean_mosum, sigma, beta, status,
                           (cudaStream_t)stream, max_mosum);
@@ -453,7 +462,11 @@ bfm_status bfm_monitor_host(bfm_design_t d, const void* Y_host, int dtype, const
             float* os = reinterpret_cast<float*>(base + L.sigma);
             float* obeta = reinterpret_cast<float*>(base + L.beta);
             uint8_t* ost = reinterpret_cast<uint8_t*>(base + L.status);
-            st = mma_supported(d, dtype, n_hist, h_frac, base + L.y, mc, nullptr)
+            const int form = auto_form(d, dtype, n_hist, h_frac, base + L.y, mc);
+            st = form == BFM_ALGO_STREAM
+                     ? launch_stream(d, dtype, base + L.y, mk, mc, n_hist, h_frac, lambda, ob, om, os, obeta, ost, cs,
+                                     nullptr)
+                 : form == BFM_ALGO_MMA
                      ? launch_mma(d, dtype, base + L.y, mk, mc, n_hist, h_frac, lambda, ob, om, os, obeta, ost, cs)
                      : launch_simt(d, base + L.y, dtype, mk, mc, n_hist, h_frac, lambda, ob, om, os, obeta, ost, cs);
         }

@@ -397,4 +397,9 @@ bfm_status bfm_batch_set_config(bfm_batch_t b, int ctas_per_sm, int grab) {
 
 int bfm_batch_tiles(bfm_batch_t b) { return b ? b->ntiles_all : 0; }
 
+int bfm_batch_form(bfm_design_t d, int dtype, int n_hist, double h_frac, const void* Y, int64_t m) {
+    if (!d || (dtype != BFM_F32 && dtype != BFM_I16) || !(n_hist >= 1 && n_hist < d->N)) return BFM_ALGO_SIMT;
+    return mma_supported(d, dtype, n_hist, h_frac, Y, m, nullptr) ? BFM_ALGO_MMA : BFM_ALGO_SIMT;
+}
+
 }  // extern "C"

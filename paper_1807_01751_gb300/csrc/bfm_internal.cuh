@@ -190,6 +190,11 @@ bfm_status launch_stream(const bfm_design_s* d, int dtype, const void* Y, const 
                          int n_hist, double h_frac, double lambda, int32_t* brk, float* mean, float* sigma,
                          float* beta, uint8_t* status, cudaStream_t stream, float* maxmo);
 cudaError_t stream_read_clear_errors(cudaStream_t s, unsigned int* bits);
+
+// The form BFM_ALGO_AUTO takes for a single call, the host-buffer entry and
+// the server: the streaming form where it applies, else the tensor-core
+// form, else the CUDA-core form.
+int auto_form(const bfm_design_s* d, int dtype, int n_hist, double h_frac, const void* Y, int64_t m);
 bfm_status launch_complete(bfm_design_s* d, int dtype, const void* Y, const uint32_t* mask, int64_t m, int n_hist,
                            double h_frac, double lambda, int32_t* brk, float* mean, float* sigma, float* beta,
                            uint8_t* status, cudaStream_t stream, float* maxmo);

@@ -196,6 +196,7 @@ __device__ __forceinline__ void simt_block(const CUtensorMap* tmap, const Monito
     phase5_resid<KH>(sp, w, S, obs, rowx, put_r, partf, putw);
     __syncthreads();
     phase6_offsets<KH>(w, S, partf);
+    __syncthreads();  // phase 7 overwrites the segment totals phase 6 reads in every warp
     int first_mon = S.n_i - S.myoff;
     first_mon = first_mon < 0 ? 0 : first_mon;
     const int jlo = __reduce_min_sync(0xffffffffu, first_mon);

@@ -213,11 +213,16 @@ void start(bfm_server_s* s, Req* q, int slot) {
         bs = cuda_fail(e, "serve: H2D");
     } else if (r.m > 0) {
         int algo = r.algo;
-        if (algo == BFM_ALGO_AUTO || algo == BFM_ALGO_MMA) {
+        if (algo == BFM_ALGO_AUTO) {
+            algo = auto_form(r.design, r.dtype, r.n_hist, r.h_frac, Y, r.m);
+        } else if (algo == BFM_ALGO_MMA) {
             const bool ok = mma_supported(r.design, r.dtype, r.n_hist, r.h_frac, Y, r.m, nullptr);
             algo = ok ? BFM_ALGO_MMA : BFM_ALGO_SIMT;
         }
-        bs = algo == BFM_ALGO_MMA
+        bs = algo == BFM_ALGO_STREAM
+                 ? launch_stream(r.design, r.dtype, Y, r.mask_bits, r.m, r.n_hist, r.h_frac, r.lambda, q->brk, q->mean,
+                                 q->sigma, q->beta, q->status, st, nullptr)
+             : algo == BFM_ALGO_MMA
                  ? launch_mma(r.design, r.dtype, Y, r.mask_bits, r.m, r.n_hist, r.h_frac, r.lambda, q->brk, q->mean, q->sigma,
                               q->beta, q->status, st)
                  : launch_simt(r.design, Y, r.dtype, r.mask_bits, r.m, r.n_hist, r.h_frac, r.lambda, q->brk, q->mean,

@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
         const float inv_scale = (fit && !degenerate) ? 1.f / (sig * sqrtf((float)np)) : 0.f;
         const float inv2 = inv_scale * inv_scale;
         const float lam2ln2 = P.lam2 * kLn2f, blg = lam2ln2 * log2f((float)np);
-        const int jlim = (int)floor(kEuler * (double)np);  // J / n_p <= e  <=>  J <= jlim
+        const float jlimf = (float)floor(kEuler * (double)np);  // J / n_p <= e  <=>  J <= jlim
 
         // pass B: the first window's h_p - 1 valid history residuals into the
         // ring (valid ranks wq .. n_p - 1 -> slots 0 .. h_p - 2), branch-free
@@ -352,15 +352,24 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
             constexpr bool full = decltype(full_c)::value;
             const int cnt = full ? G : n - d0;
             const T* st = acquire();
+            if (__any_sync(~0u, q + G > 0)) {  // some pixel of the warp may reach its window in this batch
 #pragma unroll
-            for (int u = 0; u < G; ++u) {
-                float y;
-                const float v = get(st, d0, u, cnt, full, y);
-                const float r = residual2<K>(y, sPhi + (full ? d0 + u : min(d0 + u, n - 1)) * NB, bres, lo0, lo1);
-                const bool take = v != 0.f && q >= 0;
-                if (take) ring[q * kThreads] = r;
-                W += take ? r : 0.f;
-                q += (int)v;
+                for (int u = 0; u < G; ++u) {
+                    float y;
+                    const float v = get(st, d0, u, cnt, full, y);
+                    const float r =
+                        residual2<K>(y, sPhi + (full ? d0 + u : min(d0 + u, n - 1)) * NB, bres, lo0, lo1);
+                    const bool take = v != 0.f && q >= 0;
+                    if (take) ring[q * kThreads] = r;
+                    W += take ? r : 0.f;
+                    q += v != 0.f ? 1 : 0;
+                }
+            } else {  // only count the valid observations
+#pragma unroll
+                for (int u = 0; u < G; ++u) {
+                    float y;
+                    q += get(st, d0, u, cnt, full, y) != 0.f ? 1 : 0;
+                }
             }
             release();
         };
@@ -368,7 +377,7 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
         if (d0 < n && !bad) passB(d0, std::false_type{});
 
         // pass C: the monitoring observations, branch-free per date
-        int jm = 0;         // valid monitoring observations so far (position J = n_p + 1 + jm)
+        float Jf = (float)(np + 1);  // position of the next valid monitoring observation (exact in float)
         int slot = hp - 1;  // ring slot of the next observation
         int brk = -1;
         float sh = 0.f, sl = 0.f, wmax = -INFINITY, wmin = INFINITY;
@@ -387,21 +396,20 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
                 const float r =
                     residual2<K>(y, sXm + (full ? d0 + u - n : min(d0 + u, N - 1) - n) * K, bres, lo0, lo1);
                 const float old = ring[slot * kThreads];
-                const float ro = jm > 0 ? old : 0.f;
+                const float ro = Jf > (float)(np + 1) ? old : 0.f;
                 if (take) ring[slot * kThreads] = r;
                 const int nslot = slot + 1 == hp ? 0 : slot + 1;
                 slot = take ? nslot : slot;
                 const float Wn = (W + r) - ro;
                 W = take ? Wn : W;
-                const int J = np + 1 + jm;
-                const float b2 = J > jlim ? fmaf(lam2ln2, log2_fast((float)J), -blg) : P.lam2;
+                const float b2 = Jf > jlimf ? fmaf(lam2ln2, log2_fast(Jf), -blg) : P.lam2;
                 const float c = take ? fmaf(W * W, inv2, -b2) : -1.f;
                 cv[u] = c;
                 cmax = fmaxf(cmax, c);
                 blk += take ? W : 0.f;
                 wmax = take ? fmaxf(wmax, W) : wmax;
                 wmin = take ? fminf(wmin, W) : wmin;
-                jm += (int)v;
+                Jf += v;
             }
             if (brk < 0 && cmax > 0.f) {
 #pragma unroll
@@ -416,7 +424,7 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
         if (bad) break;
         if (!active) continue;
 
-        const int Np = np + jm;
+        const int Np = (int)Jf - 1;
         if (np <= K) {
             write_unfitted(p, BFM_PX_INSUFFICIENT_HISTORY);
         } else if (!nonsingular) {

@@ -40,7 +40,9 @@ def test_batch_equals_single_calls_and_oracle(bfm):
         d = bfm.Design(t["dates"], t["k"], 23.0)
         Yd = torch.from_numpy(t["Y"]).cuda()
         outs.append(b.add(d, Yd, n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"]))
-        singles.append(bfm.monitor(d, Yd, n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"], algo=bfm.BFM_ALGO_AUTO))
+        dt = bfm.BFM_F32 if t["Y"].dtype == np.float32 else bfm.BFM_I16
+        form = bfm.bfm_batch_form(d, dt, t["n_hist"], 0.25, Yd, t["m"])
+        singles.append(bfm.monitor(d, Yd, n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"], algo=form))
     b.run()
     torch.cuda.synchronize()
     assert bfm.bfm_device_errors() == 0
@@ -60,7 +62,7 @@ def test_batch_equals_single_calls_and_oracle(bfm):
 
 def test_batch_tensor_core_variants(bfm):
     """Tiles of every harmonic order in both storage types, widths rounded to
-    multiples of 8 so that AUTO gives them the tensor-core form: the
+    multiples of 8 so that the batch gives them the tensor-core form: the
     persistent tensor-core kernels (one per variant) reproduce single calls
     bit for bit."""
     tiles = _tiles(scale=0.02, count=16, px_multiple=8)
@@ -70,10 +72,11 @@ def test_batch_tensor_core_variants(bfm):
         d = bfm.Design(t["dates"], t["k"], 23.0)
         Yd = torch.from_numpy(t["Y"]).cuda()
         dt = bfm.BFM_F32 if t["Y"].dtype == np.float32 else bfm.BFM_I16
-        if bfm.bfm_algo_auto(d, dt, t["n_hist"], 0.25, Yd, t["m"]) == bfm.BFM_ALGO_MMA:
+        form = bfm.bfm_batch_form(d, dt, t["n_hist"], 0.25, Yd, t["m"])
+        if form == bfm.BFM_ALGO_MMA:
             forms.add((t["k"], dt))
         outs.append(b.add(d, Yd, n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"]))
-        singles.append(bfm.monitor(d, Yd, n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"]))
+        singles.append(bfm.monitor(d, Yd, n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"], algo=form))
     assert len(forms) >= 4, forms
     b.run()
     b.run()
