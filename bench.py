@@ -38,9 +38,9 @@ sys.path.insert(0, ROOT)
 METRIC = "BFAST-monitor pixels/s at 8.4M px x 414 dates; p50/p99 tile latency"
 # DRAM bytes per pixel per launch from the ncu captures summarised in
 # profiles/ (None once the kernel changes after the capture).
-TRAFFIC_PER_PX = {"f32": (1.7866e9 / 1048576,), "f32simt": (None,), "f32stream": (1.8958e9 / 1048576,),
+TRAFFIC_PER_PX = {"f32": (1.7866e9 / 1048576,), "f32simt": (None,), "f32stream": (1.8983e9 / 1048576,),
                   "i16": (None,),
-                  "i16stream": (None,), "f32complete": (1.797e9 / 1048576,)}
+                  "i16stream": (None,), "f32complete": (1.7958e9 / 1048576,)}
 
 WORKLOAD = "c2: full scene 8,388,608 px x 414 dates, n_hist=228, K=8, f=23, h=0.25, plain float32"
 

@@ -244,7 +244,6 @@ __global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2)
     const int ng1 = (n + G1 - 1) / G1, ng3 = (N - n + G3 - 1) / G3, Q = 2 * ng1 + ng3;
     const int64_t my_tiles = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const int64_t total = my_tiles * Q;
-    int64_t j = 0;
     bool bad = false;
     auto issue = [&](int64_t js) {  // producer: fill the slot of stage js with one box (256 pixels x G dates)
         const int64_t tl = js / Q;
@@ -280,16 +279,22 @@ __global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2)
         }
         return;
     }
+    // the consumers' stage j kept as (slot, lap parity): slot = j % kStages, phase = (j / kStages) & 1
+    int cslot = 0;
+    uint32_t cphase = 0;
     auto acquire = [&]() -> const T* {  // wait for stage j; this thread's column in it
-        const int slot = (int)(j % kStages);
-        const bool ok = ptx::mbar_wait_bounded(full + slot, (uint32_t)((j / kStages) & 1), kWaitNs);
+        const int slot = cslot;
+        const bool ok = ptx::mbar_wait_bounded(full + slot, cphase, kWaitNs);
         if (__any_sync(~0u, !ok) || *abort_flag) bad = true;  // warp-uniform
         return reinterpret_cast<const T*>(stages + slot * kStageBytes) + threadIdx.x;
     };
     auto release = [&]() {  // this warp is done with stage j
         __syncwarp();
-        if ((threadIdx.x & 31) == 0) mbar_arrive(empty + (int)(j % kStages));
-        ++j;
+        if ((threadIdx.x & 31) == 0) mbar_arrive(empty + cslot);
+        if (++cslot == kStages) {
+            cslot = 0;
+            cphase ^= 1u;
+        }
     };
 
     int64_t tile = blockIdx.x;

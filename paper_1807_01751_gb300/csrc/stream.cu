@@ -3,8 +3,8 @@
 //
 // Each pixel's column of Y is streamed four times through shared memory
 // (pass A, A', B over the history, pass C over the monitoring dates), in
-// stages filled by 2-D TMA boxes (256 pixels x 8 float or 16 int16 dates)
-// that a producer warp issues up to kStages stages ahead; the history stays
+// stages filled by 2-D TMA boxes (256 pixels x 8 dates: three float or six
+// int16 stages) that a producer warp issues up to a full ring ahead; the history stays
 // in L2 between its passes (evict-last hints, a grid sized to the L2), so Y
 // is read once from DRAM.  Per pixel (Section 2.1, Eq. 3-6, Algorithm 1 with
 // missing values masked, as in the other forms):
@@ -56,8 +56,15 @@ cudaError_t stream_read_clear_errors(cudaStream_t s, unsigned int* bits) {
 namespace {
 
 constexpr int kThreads = 256;                // pixels per CTA (eight consumer warps)
-constexpr int kStageBytes = 8192;            // one stage: 8 (float) or 16 (int16) dates of the tile
-constexpr int kStages = 3;                   // stages in flight per CTA
+constexpr int kDates = 8;                    // dates per stage (one TMA box of 256 pixels x 8 dates)
+constexpr int kStageArea = 24576;            // bytes of stages per CTA: 3 float or 6 int16 stages
+constexpr int kMaxStages = 6;
+
+template <typename T>
+struct Stage {
+    static constexpr int kBytes = kDates * kThreads * (int)sizeof(T);
+    static constexpr int kCount = kStageArea / kBytes;
+};
 constexpr size_t kSmemMax = 112 * 1024;      // two CTAs per SM
 constexpr double kL2Budget = 80e6;           // bytes of history the resident pixels may hold in L2
 constexpr uint64_t kWaitNs = 2000000000ull;  // bound of every wait
@@ -140,8 +147,8 @@ __host__ __device__ inline Layout stream_layout(int N, int n, int K, int NB, int
     L.xm = up128(sizeof(float) * (size_t)n * NB);
     L.ring = L.xm + up128(sizeof(float) * (size_t)(N - n) * K);
     L.stages = L.ring + up128(sizeof(float) * (size_t)hmax * kThreads);
-    L.bars = L.stages + (size_t)kStages * kStageBytes;
-    L.total = L.bars + 2 * kStages * sizeof(uint64_t) + 16;
+    L.bars = L.stages + (size_t)kStageArea;
+    L.total = L.bars + 2 * kMaxStages * sizeof(uint64_t) + 16;
     return L;
 }
 
@@ -150,7 +157,9 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
     stream_kernel(const __grid_constant__ CUtensorMap tmap, const StreamParams P) {
     using B = Basis<KH>;
     constexpr int K = B::K, NB = B::NB, NBR = B::NBR;
-    constexpr int G = kStageBytes / (kThreads * (int)sizeof(T));  // dates per stage
+    constexpr int G = kDates;                    // dates per stage
+    constexpr int kStageBytes = Stage<T>::kBytes;
+    constexpr int kStages = Stage<T>::kCount;    // stages in flight
     extern __shared__ __align__(128) unsigned char smem[];
     const int n = P.n, N = P.N, hmax = P.hmax;
     const int64_t m = P.m;
@@ -160,8 +169,8 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
     float* ring = reinterpret_cast<float*>(smem + Lo.ring) + threadIdx.x;  // slot s at ring[s * kThreads]
     unsigned char* stages = smem + Lo.stages;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + Lo.bars);
-    uint64_t* empty = full + kStages;
-    volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(empty + kStages);
+    uint64_t* empty = full + kMaxStages;
+    volatile uint32_t* abort_flag = reinterpret_cast<volatile uint32_t*>(empty + kMaxStages);
     for (int i = threadIdx.x; i < n * NB; i += blockDim.x) sPhi[i] = P.basis[i];
     for (int i = threadIdx.x; i < (N - n) * K; i += blockDim.x) {
         const int r = i / K;
@@ -216,18 +225,23 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
         return;
     }
 
-    int64_t j = 0;
     bool bad = false;
+    // the consumers' stage j kept as (slot, lap parity): slot = j % kStages, phase = (j / kStages) & 1
+    int cslot = 0;
+    uint32_t cphase = 0;
     auto acquire = [&]() -> const T* {  // wait for stage j; this thread's column in it
-        const int slot = (int)(j % kStages);
-        const bool ok = ptx::mbar_wait_bounded(full + slot, (uint32_t)((j / kStages) & 1), kWaitNs);
+        const int slot = cslot;
+        const bool ok = ptx::mbar_wait_bounded(full + slot, cphase, kWaitNs);
         if (__any_sync(~0u, !ok) || *abort_flag) bad = true;  // warp-uniform
         return reinterpret_cast<const T*>(stages + slot * kStageBytes) + threadIdx.x;
     };
     auto release = [&]() {  // this warp is done with stage j
         __syncwarp();
-        if ((threadIdx.x & 31) == 0) mbar_arrive(empty + (int)(j % kStages));
-        ++j;
+        if ((threadIdx.x & 31) == 0) mbar_arrive(empty + cslot);
+        if (++cslot == kStages) {
+            cslot = 0;
+            cphase ^= 1u;
+        }
     };
     const float qnan = __int_as_float(0x7fc00000);
     auto write_unfitted = [&](int64_t p, int st) {
@@ -559,7 +573,7 @@ bfm_status launch_stream(const bfm_design_s* d, int dtype, const void* Y, const 
     std::memset(&tm, 0, sizeof tm);
     const cuuint64_t gdim[2] = {(cuuint64_t)m, (cuuint64_t)d->N};
     const cuuint64_t gstride[1] = {(cuuint64_t)m * elt};
-    const cuuint32_t box[2] = {(cuuint32_t)kThreads, (cuuint32_t)(kStageBytes / (kThreads * elt))};
+    const cuuint32_t box[2] = {(cuuint32_t)kThreads, (cuuint32_t)kDates};
     const cuuint32_t es[2] = {1u, 1u};
     if (enc(&tm, elt == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 2,
             const_cast<void*>(Y), gdim, gstride, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
