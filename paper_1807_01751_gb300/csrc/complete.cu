@@ -38,6 +38,7 @@
 
 #include "bfm_internal.cuh"
 #include "ptx.cuh"
+#include "stage.cuh"
 
 namespace bfm {
 
@@ -56,6 +57,8 @@ cudaError_t complete_read_clear_errors(cudaStream_t s, unsigned int* bits) {
 }
 
 namespace {
+
+using namespace stage;
 
 constexpr int kThreads = 256;
 constexpr int kU1 = 16;  // history dates per load batch (16 loads in flight per thread)
@@ -81,24 +84,6 @@ struct CompleteParams {
     uint8_t* status;
     float* maxmo;
 };
-
-__device__ __forceinline__ uint64_t policy_evict_last() {
-    uint64_t pol;
-    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-
-__device__ __forceinline__ uint64_t policy_evict_normal() {
-    uint64_t pol;
-    asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-
-__device__ __forceinline__ uint64_t policy_evict_first() {
-    uint64_t pol;
-    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
 
 // One stored value with an L2 policy (no use of the result here, so that a
 // batch of these loads is in flight together).
@@ -130,22 +115,6 @@ __device__ __forceinline__ void comp_add(float& hi, float& lo, float x) {
     hi = s;
 }
 
-template <int K>
-__device__ __forceinline__ float residual(float y, const float* x, const float (&beta)[K]) {
-    float yhat = 0.f;
-#pragma unroll
-    for (int a = 0; a < K; ++a) yhat = fmaf(x[a], beta[a], yhat);
-    return y - yhat;
-}
-
-// Residual with the intercept and trend coefficients held as hi + lo (lo the
-// refinement step): the rounding of those two to float would otherwise enter
-// every residual of a window with the same sign, h times over.
-template <int K>
-__device__ __forceinline__ float residual2(float y, const float* x, const float (&beta)[K], float lo0, float lo1) {
-    return residual<K>(y, x, beta) - fmaf(x[1], lo1, lo0);
-}
-
 // Shared-memory layout of one CTA: M' [n][K], X [N][K], the squared boundary
 // [N - n] and the window sums of the regressors [K] (floats); then, in the
 // staged form, 128-byte aligned: the last h residuals of each thread
@@ -153,21 +122,6 @@ __device__ __forceinline__ float residual2(float y, const float* x, const float 
 // and empty mbarriers, and an abort flag.
 __host__ __device__ inline size_t ring_offset(int N, int n, int K) {
     return ((size_t)(n + N) * K + (size_t)(N - n) + (size_t)K + 31) & ~(size_t)31;  // 128-byte aligned
-}
-
-// 2-D tiled TMA load of the box at (x = pixel, y = date) completing on `bar`,
-// with an L2 policy.
-__device__ __forceinline__ void tma_load_2d_hint(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
-                                                 uint64_t pol) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(ptx::smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(ptx::smem_u32(bar)), "l"(pol)
-        : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(ptx::smem_u32(bar)) : "memory");
 }
 
 // kStaged: Y reaches the threads through shared-memory stages filled by 1-D
@@ -218,7 +172,7 @@ __global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2)
     }
     __syncthreads();
     const float qnan = __int_as_float(0x7fc00000);
-    const uint64_t keep = policy_evict_last(), normal = policy_evict_normal(), drop = policy_evict_first();
+    const uint64_t keep = l2_evict_last(), normal = l2_evict_normal(), drop = l2_evict_first();
     const int64_t ntiles = (m + kThreads - 1) / kThreads;
     auto write_unfitted = [&](int64_t p, int st) {
         P.brk[p] = -1;
@@ -256,7 +210,7 @@ __global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2)
         const uint64_t pol = k < ng1 ? keep : (k < 2 * ng1 ? drop : normal);
         // pixels past m and dates past N arrive as zeros; the box is always full
         ptx::mbar_arrive_expect_tx(full + slot, (uint32_t)kStageBytes);
-        tma_load_2d_hint(stages + slot * kStageBytes, &tmap, full + slot, px0, d0, pol);
+        tma_box(stages + slot * kStageBytes, &tmap, full + slot, px0, d0, pol);
     };
     if (kStaged && threadIdx.x >= kThreads) {  // the producer warp: one lane issues
         if (threadIdx.x == kThreads) {
@@ -541,20 +495,6 @@ bfm_status launch_kh(const CUtensorMap& tm, const CompleteParams& P, int dtype, 
                   : launch_variant<KH, int16_t, false, kStaged>(tm, P, grid, smem, st);
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* ptr = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
-    });
-    return fn;
-}
-
 // The shared table of (design, n_hist): M' and X in float, built in FP64.
 // Status BFM_PX_INSUFFICIENT_HISTORY for n <= K, BFM_PX_SINGULAR when a
 // Cholesky pivot of X_h'X_h falls below 1e-5 of its diagonal entry (the rank
@@ -688,7 +628,7 @@ bfm_status launch_complete(bfm_design_s* d, int dtype, const void* Y, const uint
     CUtensorMap tm;
     std::memset(&tm, 0, sizeof tm);
     if (staged) {  // Y as a 2-D tensor (pixels innermost), boxes of 256 pixels x one stage of dates
-        auto enc = encode_fn();
+        auto enc = encode_tiled();
         const cuuint64_t gdim[2] = {(cuuint64_t)m, (cuuint64_t)d->N};
         const cuuint64_t gstride[1] = {(cuuint64_t)m * elt};
         const cuuint32_t box[2] = {(cuuint32_t)kThreads, (cuuint32_t)(kStageBytes / (kThreads * elt))};

@@ -36,6 +36,7 @@
 #include "bfm_internal.cuh"
 #include "ptx.cuh"
 #include "simt_seg.cuh"
+#include "stage.cuh"
 
 namespace bfm {
 
@@ -54,6 +55,8 @@ cudaError_t stream_read_clear_errors(cudaStream_t s, unsigned int* bits) {
 }
 
 namespace {
+
+using namespace stage;
 
 constexpr int kThreads = 256;                // pixels per CTA (eight consumer warps)
 constexpr int kDates = 8;                    // dates per stage (one TMA box of 256 pixels x 8 dates)
@@ -84,30 +87,6 @@ struct StreamParams {
     float* maxmo;
 };
 
-__device__ __forceinline__ uint64_t policy(int kind) {
-    uint64_t pol;
-    if (kind == 0)
-        asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-    else if (kind == 1)
-        asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(pol));
-    else
-        asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-
-__device__ __forceinline__ void tma_box(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
-                                        uint64_t pol) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(ptx::smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(ptx::smem_u32(bar)), "l"(pol)
-        : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(ptx::smem_u32(bar)) : "memory");
-}
-
 // Observation value and validity (float: NaN missing; int16: -32768 missing).
 __device__ __forceinline__ bool obs(float raw, float& y) {
     y = raw;
@@ -116,20 +95,6 @@ __device__ __forceinline__ bool obs(float raw, float& y) {
 __device__ __forceinline__ bool obs(int16_t raw, float& y) {
     y = (float)raw;
     return raw != (int16_t)-32768;
-}
-
-template <int K>
-__device__ __forceinline__ float residual(float y, const float* x, const float (&beta)[K]) {
-    float yhat = 0.f;
-#pragma unroll
-    for (int a = 0; a < K; ++a) yhat = fmaf(x[a], beta[a], yhat);
-    return y - yhat;
-}
-
-// Residual with the intercept and trend coefficients as hi (beta) + lo (lo0, lo1).
-template <int K>
-__device__ __forceinline__ float residual2(float y, const float* x, const float (&beta)[K], float lo0, float lo1) {
-    return residual<K>(y, x, beta) - fmaf(x[1], lo1, lo0);
 }
 
 // Shared-memory layout (bytes, each part 128-byte aligned): basis rows of the
@@ -197,7 +162,7 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
     if (threadIdx.x >= kThreads) {  // the producer warp: one lane issues the boxes
         if (threadIdx.x == kThreads) {
             ptx::prefetch_tmap(&tmap);
-            const uint64_t keep = policy(0), normal = policy(1), drop = policy(2);
+            const uint64_t keep = l2_evict_last(), normal = l2_evict_normal(), drop = l2_evict_first();
             int64_t js = 0;
             for (; js < total; ++js) {
                 const int slot = (int)(js % kStages);
@@ -508,20 +473,6 @@ bfm_status launch_kh(const CUtensorMap& tm, const StreamParams& P, int dtype, in
                   : launch_one<KH, int16_t, false>(tm, P, grid, smem, st);
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* ptr = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
-    });
-    return fn;
-}
-
 int stream_hmax(int n_hist, double h_frac) {
     int h = (int)std::floor(h_frac * (double)n_hist);
     return h < 1 ? 1 : (h > n_hist ? n_hist : h);
@@ -545,7 +496,7 @@ bfm_status launch_stream(const bfm_design_s* d, int dtype, const void* Y, const 
                   "within 112 KB of shared memory");
         return BFM_EUNSUPPORTED;
     }
-    auto enc = encode_fn();
+    auto enc = encode_tiled();
     if (!enc) {
         set_error("bfm_monitor (stream): cuTensorMapEncodeTiled is not available");
         return BFM_ECUDA;
