@@ -353,7 +353,12 @@ bfm_status bfm_batch_destroy(bfm_batch_t b);
  * Request fields: design (kept alive by the caller), Y (host when y_on_host,
  * page-locked for the copy to overlap; else device), dtype, mask_bits
  * (device or NULL), m, n_hist, h_frac, lambda as bfm_monitor; algo as
- * bfm_monitor_ex (AUTO picks the tensor-core form when it applies).
+ * bfm_monitor_ex (AUTO picks the streaming form, else the tensor-core form,
+ * else the CUDA-core form; BFM_ALGO_MMA falls back to the CUDA-core form
+ * when the tensor-core form does not take the request; an explicit
+ * BFM_ALGO_STREAM the form does not take fails the request with
+ * BFM_EUNSUPPORTED).  bfm_serve_submit returns BFM_EINVAL for an algo
+ * outside the bfm_algo values.
  */
 typedef struct bfm_server_s *bfm_server_t;
 typedef struct {

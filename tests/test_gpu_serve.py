@@ -119,3 +119,28 @@ def test_refusals_and_cancellation(bfm):
         if st == "done":
             _same(srv.result(k, d.K, tiles[0]["m"]), ref)
     srv.close()
+
+
+def test_explicit_forms_and_bad_algo(bfm):
+    """A request with an explicit form: the complete-series form on a cloud-free tile equals a direct
+    bfm_monitor call with that form; an algo outside the bfm_algo values is refused at submit."""
+    d_, Y, _ = synth.scene(seed=31, m=2048, N=228, n_hist=100, f=23.0, k_gen=2, intercept=0.5, slope=0.001,
+                           coef_fixed=[0.2, 0.0, 0.0, 0.05], noise_sd=0.03, miss="none", break_frac=0.2,
+                           step=(-0.3, -0.3), dtype="f32")
+    d = bfm.Design(d_, 3, 23.0)
+    Yd = torch.from_numpy(Y).cuda()
+    lam = synth.workload_lambda("c1")
+    srv = bfm.Server(hbm_budget=1 << 28, slots=2)
+    for algo in (bfm.BFM_ALGO_COMPLETE, bfm.BFM_ALGO_STREAM, bfm.BFM_ALGO_SIMT):
+        k = srv.submit(d, Yd, n_hist=100, h_frac=0.25, lam=lam, algo=algo)
+        srv.wait_all(60)
+        st, _, rc = srv.poll(k)
+        assert st == "done" and rc == 0
+        direct = bfm.monitor(d, Yd, n_hist=100, h_frac=0.25, lam=lam, algo=algo)
+        torch.cuda.synchronize()
+        _same(srv.result(k, d.K, 2048), direct)
+        srv.release(k)
+    with pytest.raises(bfm.BfmError) as ei:
+        srv.submit(d, Yd, n_hist=100, h_frac=0.25, lam=lam, algo=7)
+    assert ei.value.code == 1
+    srv.close()
