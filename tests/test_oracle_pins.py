@@ -351,3 +351,29 @@ def test_max_mosum_definition():
     assert out["status"][3] == 1 and np.isnan(mx[3])
     ok = out["status"] == 0
     assert np.all(np.abs(mx[ok]) == np.nanmax(np.abs(tr[ok]), axis=1))
+
+
+def test_shared_pseudo_inverse_on_complete_series():
+    """Section 3, Eq. 8-11: without missing values every pixel shares the history design, so
+    beta_all = M Y_h with one M = (X_h'X_h)^-1 X_h' (built here with numpy's pinv, independently
+    of the oracle), the predictions are X beta_all and the residuals Y - X beta_all.  The oracle's
+    per-pixel Householder fits, sigma-hat and MOSUM means must agree with that matrix algebra."""
+    d, Y, _ = synth.scene(seed=9, m=64, N=120, n_hist=60, f=23.0, k_gen=2, intercept=0.5, slope=0.002,
+                          coef_fixed=[0.2, 0.0, 0.0, 0.05], noise_sd=0.03, miss="none", break_frac=0.3,
+                          step=(-0.3, -0.3), dtype="f32")
+    n, h_frac, lam, k = 60, 0.25, 1.9, 2
+    ref = oracle.monitor(d, Y, k=k, f=23.0, n_hist=n, h_frac=h_frac, lam=lam)
+    X = _design_np(d, k, 23.0)
+    Yd = Y.astype(np.float64)
+    M = np.linalg.pinv(X[:n])                      # K x n, shared by every pixel
+    B = M @ Yd[:n]                                 # K x m: beta_all = M Y_h
+    R = Yd - X @ B                                 # residuals of every date
+    K = X.shape[1]
+    sig = np.sqrt((R[:n] ** 2).sum(axis=0) / (n - K))
+    h = int(math.floor(h_frac * n))
+    cs = np.vstack([np.zeros((1, Yd.shape[1])), np.cumsum(R, axis=0)])
+    mo = np.array([(cs[j] - cs[j - h]) / (sig * math.sqrt(n)) for j in range(n + 1, Y.shape[0] + 1)])
+    assert (ref["status"] == 0).all()
+    np.testing.assert_allclose(ref["beta"], B, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(ref["sigma"], sig, rtol=1e-9)
+    np.testing.assert_allclose(ref["mean_mosum"], mo.mean(axis=0), rtol=1e-9, atol=1e-12)
