@@ -75,11 +75,6 @@ class Arena {
         }
     }
     size_t size() const { return size_; }
-    size_t largest() const {
-        size_t b = 0;
-        for (auto& kv : free_) b = std::max(b, kv.second);
-        return b;
-    }
 
   private:
     size_t size_ = 0;
