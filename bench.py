@@ -52,6 +52,23 @@ def _dist():
     return ws, rank, local
 
 
+def slowest_rank(x: float, device) -> float:
+    """The largest value of x over the ranks (a job's time is its slowest
+    rank's); x itself when there is one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, steps: int, world_size: int, total_ms: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world_size * units_per_rank * steps / (total_ms / 1e3)
+
+
 def _peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -316,17 +333,13 @@ def run_ours(args):
             dist.barrier()
         clk = clocks.stop()
         per = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
-        total_ms = evs[0].elapsed_time(evs[-1])
-        if ws > 1:
-            t = torch.tensor([total_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = slowest_rank(evs[0].elapsed_time(evs[-1]), dev)
         elt = 2 if form.startswith("i16") else 4
         alg_bytes = N * m * elt + m * (4 + 4 + 4 + 4 * K + 1)
         achieved = alg_bytes / (statistics.mean(per) / 1e3) / 1e9
         srt = sorted(per)
         del Yf
-        return {"value": ws * m * args.steps / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
+        return {"value": job_rate(m, args.steps, ws, total_ms), "ms_per_step": total_ms / args.steps,
                 "latency_ms": {"p50": srt[len(srt) // 2],
                                "p99": srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)],
                                "unit": "one full-scene call"},
@@ -373,12 +386,8 @@ def run_ours(args):
             hstep()
         e1.record(stream)
         torch.cuda.synchronize()
-        e_ms = e0.elapsed_time(e1) / e_steps
-        if ws > 1:
-            t = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": ws * m / (e_ms / 1e3), "unit": "pixels/s", "h2d_bytes_per_step": N * m * e_elt,
+        e_ms = slowest_rank(e0.elapsed_time(e1) / e_steps, dev)
+        e2e = {"value": job_rate(m, 1, ws, e_ms), "unit": "pixels/s", "h2d_bytes_per_step": N * m * e_elt,
                "d2h_bytes_per_step": m * (4 + 4 + 4 + 4 * K + 1), "ms_per_step": e_ms,
                "api": "bfm_monitor_host (pinned host Y and outputs, 1 Mi-pixel chunks)"}
         Ysrc = Yh
