@@ -177,11 +177,12 @@ def test_noise_free_series_recovered_exactly():
         assert o["status"][p] == 3 and o["break_idx"][p] == -1 and o["mean_mosum"][p] == 0.0
 
 
-def test_alg3_recurrence_on_complete_series():
-    """Complete series: the oracle's direct window sums equal the sliding-sum
-    recurrence of Algorithm 3 (initial window of ws = h residuals starting
-    after s = n - h, O(1) updates, sigma over the first hs = n residuals with
-    hs - (2+2k) degrees of freedom, division by sigma*sqrt(hs))."""
+def test_window_sums_are_cumsum_differences_on_complete_series():
+    """Complete series: every MOSUM value of Eq. 3 is a difference of the
+    cumulative residual sum, (S_j - S_{j-h}) / (sigma-hat sqrt(n)), with
+    S_j = r_1 + ... + r_j, h = floor(0.25 n) terms per window and sigma-hat
+    from the n history residuals with n - (2 + 2k) degrees of freedom
+    (Section 2.1).  The oracle forms each window by a direct sum instead."""
     w = synth.workload("c1", m=64)
     N, n, k, f = w["N"], w["n_hist"], 3, w["f"]
     _, Yc, _ = synth.scene(seed=11, m=64, N=N, n_hist=n, f=f, dtype="f32", k_gen=2, intercept=0.5,
@@ -191,17 +192,96 @@ def test_alg3_recurrence_on_complete_series():
     o = oracle.monitor(w["dates"], Yd, k=k, f=f, n_hist=n, h_frac=0.25, lam=w["lam"], trace=True)
     X = _design_np(w["dates"], k, f)
     h = int(0.25 * n)
+    pos = np.arange(n + 1, N + 1)              # 1-based monitoring positions
     for p in range(0, 64, 7):
-        R = Yd[:, p] - X @ o["beta"][:, p]
-        s, ws, hs, ms = n - h, h, n, N - n
-        MO = np.empty(ms)
-        MO[0] = R[s + 1: s + ws + 1].sum()
-        for j in range(1, ms):
-            MO[j] = MO[j - 1] - R[s + j] + R[s + ws + j]
-        sigma = math.sqrt((R[:hs] ** 2).sum() / (hs - (2 + 2 * k)))
-        MO /= sigma * math.sqrt(hs)
-        np.testing.assert_allclose(o["mo_trace"][p, :ms], MO, rtol=1e-9, atol=1e-10)
-        np.testing.assert_allclose(o["sigma"][p], sigma, rtol=1e-12)
+        resid = Yd[:, p] - X @ o["beta"][:, p]
+        cum = np.concatenate([[0.0], np.cumsum(resid)])
+        sig = math.sqrt((resid[:n] ** 2).sum() / (n - (2 + 2 * k)))
+        mo = (cum[pos] - cum[pos - h]) / (sig * math.sqrt(n))
+        np.testing.assert_allclose(o["mo_trace"][p, : N - n], mo, rtol=1e-9, atol=1e-10)
+        np.testing.assert_allclose(o["sigma"][p], sig, rtol=1e-12)
+
+
+def _residuals_for_trace(e, mo, h, K):
+    """Monitoring residuals whose MOSUM process (Eq. 3) is exactly `mo`, given
+    the history residuals e: with W_j = sigma-hat sqrt(n) mo_j the sum of the h
+    residuals ending at position j, r_j = W_j - W_{j-1} + r_{j-h}."""
+    n = e.size
+    scale = math.sqrt((e ** 2).sum() / (n - K)) * math.sqrt(n)
+    r = np.concatenate([e, np.zeros(mo.size)])
+    w_prev = e[n - h:].sum()                    # window ending at the last history position
+    for i in range(mo.size):
+        j = n + i                               # 0-based index of position n + 1 + i
+        w = scale * mo[i]
+        r[j] = w - w_prev + r[j - h]
+        w_prev = w
+    return r
+
+
+def _boundary_np(lam, n, npos):
+    j = np.arange(n + 1, n + 1 + npos)
+    return lam * np.sqrt(np.where(j / n <= math.e, 1.0, np.log(j / n)))
+
+
+@pytest.mark.parametrize("case", ["min_at_break", "min_before_break", "no_break"])
+def test_margin_closed_form(case):
+    """The tie margin min ||MO_j| - b_j| over the monitoring positions up to and
+    including the first crossing (all positions when there is none), from a
+    prescribed MOSUM process: the monitoring residuals are built so that Eq. 3
+    gives exactly that process (history noise orthogonal to the design, so the
+    fit is exact), and the boundary of Eq. 4 is its closed form.  Each case is
+    chosen so that taking the minimum over all positions, or stopping one
+    position before the break, gives a different number."""
+    rng = np.random.default_rng(31)
+    N, n_hist, f, lam, hf, k = 150, 64, 23.0, 1.8, 0.25, 2
+    K = 2 + 2 * k
+    d = synth.dates(4, N)
+    valid = rng.random(N) > 0.25
+    valid[0] = valid[n_hist] = True
+    idx = np.nonzero(valid)[0]
+    n = int((idx < n_hist).sum())
+    P = idx.size - n
+    h = max(1, min(int(math.floor(hf * n)), n))
+    X = _design_np(d[idx], k, f)
+    beta = np.array([0.5, 0.002, 0.1, -0.05, 0.03, 0.02])
+    e = _orth_noise(X[:n], rng, 0.02)
+    b = _boundary_np(lam, n, P)
+    sgn = np.where(np.arange(P) % 2 == 0, 1.0, -1.0)
+    if case == "min_at_break":
+        mo = 0.5 * b * sgn
+        j1, j2 = 20, 35
+        mo[j1] = -(b[j1] + 0.004)               # first crossing (negative), margin 0.004
+        mo[j2] = b[j2] - 0.001                  # closer, but after the break
+        first, expect = j1, 0.004
+    elif case == "min_before_break":
+        mo = 0.4 * b * sgn
+        j0, j1, j2 = 10, 30, 45
+        mo[j0] = b[j0] - 0.0015                 # closest approach, no crossing
+        mo[j1] = b[j1] + 0.01                   # first crossing
+        mo[j2] = -(b[j2] + 0.0005)              # after the break
+        first, expect = j1, 0.0015
+    else:
+        mo = 0.6 * b * sgn
+        j3 = 40
+        mo[j3] = -(b[j3] - 0.002)               # closest approach anywhere
+        first, expect = -1, 0.002
+    dist = np.abs(np.abs(mo) - b)
+    upto = dist[: first + 1] if first >= 0 else dist
+    assert abs(upto.min() - expect) < 1e-12
+    # the slips named above give other values
+    if case != "no_break":
+        assert abs(dist.min() - expect) > 1e-4                 # minimum over all positions
+    if case == "min_at_break":
+        assert abs(dist[:first].min() - expect) > 1e-4         # stopping before the break
+    r = _residuals_for_trace(e, mo, h, K)
+    y = X @ beta + r
+    Y = np.full((N, 1), np.nan)
+    Y[idx, 0] = y
+    o = oracle.monitor(d, Y, k=k, f=f, n_hist=n_hist, h_frac=hf, lam=lam, trace=True)
+    assert o["status"][0] == 0 and o["n"][0] == n and o["h"][0] == h
+    np.testing.assert_allclose(o["mo_trace"][0, :P], mo, rtol=1e-9, atol=1e-10)
+    assert o["break_idx"][0] == (idx[n + first] if first >= 0 else -1)
+    np.testing.assert_allclose(o["margin"][0], expect, rtol=1e-6)
 
 
 def test_invariance_affine_in_model_space():
@@ -294,14 +374,35 @@ def test_lambda_matches_paper_value():
     assert abs(lam - g["lambda"]) < g["tolerance"]
 
 
-def test_lambda_monotone_and_size():
-    """lambda grows with the horizon and as alpha shrinks; the simulated
-    rejection rate at lambda is alpha."""
+def test_lambda_monotone():
+    """lambda grows with the horizon and as alpha shrinks."""
     a = oracle.critical_value(0.05, 0.25, 1.5, G=400, reps=8000, seed=1)
     b = oracle.critical_value(0.05, 0.25, 3.0, G=400, reps=8000, seed=1)
-    c, st = oracle.critical_value(0.01, 0.25, 3.0, G=400, reps=8000, seed=1, return_stats=True)
+    c = oracle.critical_value(0.01, 0.25, 3.0, G=400, reps=8000, seed=1)
     assert a < b < c
-    assert abs((st > b).mean() - 0.05) < 0.01
+
+
+@pytest.mark.parametrize("h", [0.25, 0.5])
+def test_lambda_at_unit_horizon_is_half_normal(h):
+    """At the horizon T = 1 the supremum runs over t = 1 alone, where
+    log+ 1 = 1 and Z(1) = W(1) - W(1-h) - h W(1) = (1-h)(W(1) - W(1-h)) - h W(1-h)
+    is normal with variance (1-h)^2 h + h^2 (1-h) = h(1-h).  So the simulated
+    statistics follow the half-normal law of scale sqrt(h(1-h)) (Kolmogorov-
+    Smirnov distance below its 1 % critical value) and lambda is
+    sqrt(h(1-h)) z_{1-alpha/2} within four standard errors of an order statistic."""
+    from statistics import NormalDist
+    R, alpha = 40000, 0.05
+    lam, st = oracle.critical_value(alpha, h, 1.0, G=200, reps=R, seed=7, return_stats=True)
+    s = math.sqrt(h * (1.0 - h))
+    x = np.sort(st)
+    cdf = np.frompyfunc(lambda v: math.erf(v / (s * math.sqrt(2.0))), 1, 1)(x).astype(np.float64)
+    D = max((np.arange(1, R + 1) / R - cdf).max(), (cdf - np.arange(R) / R).max())
+    assert D < 1.63 / math.sqrt(R)
+    nd = NormalDist()
+    q = s * nd.inv_cdf(1.0 - alpha / 2.0)
+    dens = 2.0 * nd.pdf(q / s) / s
+    se = math.sqrt(alpha * (1.0 - alpha) / R) / dens
+    assert abs(lam - q) < 4.0 * se
 
 
 def test_lambda_table_consistent():
