@@ -406,8 +406,11 @@ bfm_status bfm_serve_destroy(bfm_server_t s);
  *           caller owns, designs stay alive until the work is done).
  *   ntiles  0 <= ntiles <= BFM_STATIC_MAX_TILES; more is BFM_EINVAL with a
  *           message (split the batch).
- *   stream  work is enqueued on it: a copy of the tile table into the fixed
- *           array, a reset of its work counter, the persistent kernel.
+ *   stream  work is enqueued on it: a small kernel that writes the tile table
+ *           into the fixed array and resets its work counter, then the
+ *           persistent kernel.  The table travels as that kernel's argument,
+ *           so the call does not wait for earlier work in `stream`, and
+ *           nothing of it refers to host memory once it returns.
  * Results equal those of bfm_monitor with BFM_ALGO_SIMT on each tile alone.
  * The first call on a device looks up the array's device address; make that
  * first call before any stream capture on the device.  Every call on a device
@@ -436,6 +439,21 @@ bfm_status bfm_batch_run_static(const bfm_tile_spec *tiles, int ntiles, void *st
 /* Reads and clears the library's device error word (bit 0: a tile load wait
  * gave up).  Synchronises `stream`. */
 bfm_status bfm_device_errors(void *stream, uint32_t *bits);
+
+/*
+ * bfm_stage_wait_limit -- the bound, in nanoseconds, of the waits in which
+ * the streaming form's (BFM_ALGO_STREAM) pixel warps wait for a stage of Y to
+ * land in shared memory.  The paper has no counterpart: every wait of the
+ * library is bounded so that a stalled copy ends the kernel with an error
+ * instead of hanging the GPU, and this setter lets a test make such a wait run
+ * out.  A wait that runs out stops its warp: the warp's pixels from that tile
+ * on get BFM_PX_TIMEOUT, bit 0 of the device error word (bfm_device_errors) is
+ * set, and the CTA's loader stops issuing copies and lets those in flight land
+ * before the CTA ends.  A bound below 1000 ns makes each wait look at its
+ * barrier once.  Process-wide; read at each launch; 0 restores the default of
+ * 2 s.  The loader's own waits keep their 2 s bound.
+ */
+bfm_status bfm_stage_wait_limit(uint64_t consumer_wait_ns);
 
 #ifdef __cplusplus
 }

@@ -8,7 +8,8 @@
 // every other stream.  For them this entry point keeps everything the
 // persistent kernel needs beyond the caller's inputs and outputs -- the tile
 // table, the tensor maps and the work counter -- in one fixed array that is
-// part of the library's device image.
+// part of the library's device image.  A small kernel, given the table as its
+// argument, writes it there ahead of the persistent kernel.
 #include <cuda.h>
 
 #include <cstring>
@@ -36,6 +37,25 @@ constexpr size_t kScratchBytes = kCounterOff + 256;
 
 // The scratch: every device that loads the library holds it until exit.
 static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
+
+// The tile table and tensor maps of one call, passed by value as the argument
+// of the kernel that writes them into the scratch: the launch copies them, so
+// nothing of the call refers to host memory once it returns, and the host does
+// not wait for earlier work in the stream (a copy from pageable host memory
+// would).
+struct StaticTable {
+    uint4 w[kCounterOff / 16];
+};
+static_assert(kCounterOff % 16 == 0, "table size must be a multiple of 16 bytes");
+static_assert(sizeof(StaticTable) <= 32000, "the table must fit the kernel argument space");
+
+// Device code names the scratch directly; it overwrites the table and clears
+// the work counter, which the previous call left behind.
+__global__ void fill_static_table(const __grid_constant__ StaticTable t) {
+    uint4* dst = reinterpret_cast<uint4*>(g_static_scratch);
+    for (int i = threadIdx.x; i < (int)(kCounterOff / 16); i += blockDim.x) dst[i] = t.w[i];
+    if (threadIdx.x == 0) *reinterpret_cast<unsigned long long*>(g_static_scratch + kCounterOff) = 0ull;
+}
 
 std::mutex g_mu;
 unsigned char* g_scratch_ptr[64] = {};  // device address of g_static_scratch, per device
@@ -134,8 +154,10 @@ extern "C" bfm_status bfm_batch_run_static(const bfm_tile_spec* tiles, int ntile
     cudaStream_t st = (cudaStream_t)stream;
     // The array keeps the previous call's contents: overwrite the table and
     // clear the work counter, in stream order before the kernel.
-    e = cudaMemcpyAsync(base, host, kCounterOff, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + kCounterOff, 0, sizeof(unsigned long long), st);
+    StaticTable table;
+    std::memcpy(&table, host, sizeof table);
+    fill_static_table<<<1, 256, 0, st>>>(table);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "bfm_batch_run_static: filling the static scratch");
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
