@@ -109,6 +109,8 @@ def load(build_if_missing: bool = True):
         lib.bfm_monitor_host.restype = i32
         lib.bfm_device_errors.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32)]
         lib.bfm_device_errors.restype = i32
+        lib.bfm_stage_wait_limit.argtypes = [ctypes.c_uint64]
+        lib.bfm_stage_wait_limit.restype = i32
         lib.bfm_batch_create.argtypes = [ctypes.POINTER(vp)]
         lib.bfm_batch_create.restype = i32
         lib.bfm_batch_add.argtypes = [vp, vp, vp, i32, vp, i64, i32, dbl, dbl, vp, vp, vp, vp, vp,
@@ -262,6 +264,11 @@ def bfm_device_errors(stream=None) -> int:
     v = ctypes.c_uint32(0)
     _check(load().bfm_device_errors(_stream(stream), ctypes.byref(v)))
     return v.value
+
+
+def bfm_stage_wait_limit(consumer_wait_ns: int) -> None:
+    """Bound of the streaming form's consumer-side stage waits (0: default 2 s)."""
+    _check(load().bfm_stage_wait_limit(int(consumer_wait_ns)))
 
 
 def bfm_batch_create() -> int:

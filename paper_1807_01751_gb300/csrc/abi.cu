@@ -493,6 +493,11 @@ bfm_status bfm_monitor_host(bfm_design_t d, const void* Y_host, int dtype, const
     return BFM_OK;
 }
 
+bfm_status bfm_stage_wait_limit(uint64_t consumer_wait_ns) {
+    set_stage_wait_ns(consumer_wait_ns);
+    return BFM_OK;
+}
+
 bfm_status bfm_device_errors(void* stream, uint32_t* bits) {
     if (!bits) {
         set_error("bfm_device_errors: bits is NULL");

@@ -190,6 +190,9 @@ bfm_status launch_stream(const bfm_design_s* d, int dtype, const void* Y, const 
                          int n_hist, double h_frac, double lambda, int32_t* brk, float* mean, float* sigma,
                          float* beta, uint8_t* status, cudaStream_t stream, float* maxmo);
 cudaError_t stream_read_clear_errors(cudaStream_t s, unsigned int* bits);
+// Bound of the staged forms' consumer-side stage waits (bfm_stage_wait_limit).
+uint64_t stage_wait_ns();
+void set_stage_wait_ns(uint64_t ns);
 
 // The form BFM_ALGO_AUTO takes for a single call, the host-buffer entry and
 // the server: the streaming form where it applies, else the tensor-core

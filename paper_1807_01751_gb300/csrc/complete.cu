@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2)
             for (; js < total; ++js) {
                 const int slot = (int)(js % kStages);
                 if (js >= kStages &&
-                    !ptx::mbar_wait_bounded(empty + slot, (uint32_t)(((js / kStages) - 1) & 1), kWaitNs)) {
+                    !wait_released(empty + slot, (uint32_t)(((js / kStages) - 1) & 1), abort_flag, kWaitNs)) {
                     *abort_flag = 1u;
                     atomicOr(&g_bfm_complete_err, 1u);
                     break;
@@ -236,10 +236,22 @@ __global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2)
     // the consumers' stage j kept as (slot, lap parity): slot = j % kStages, phase = (j / kStages) & 1
     int cslot = 0;
     uint32_t cphase = 0;
-    auto acquire = [&]() -> const T* {  // wait for stage j; this thread's column in it
+    // Wait for stage j: this thread's column in it, or nullptr when the wait
+    // gave up or the CTA is aborting (warp-uniform).  A warp that gives up
+    // neither reads nor releases the stage, so the producer never refills a
+    // slot whose copy may still be in flight; it raises the abort flag at once.
+    auto acquire = [&]() -> const T* {
         const int slot = cslot;
         const bool ok = ptx::mbar_wait_bounded(full + slot, cphase, kWaitNs);
-        if (__any_sync(~0u, !ok) || *abort_flag) bad = true;  // warp-uniform
+        const bool gave_up = __any_sync(~0u, !ok);
+        if (gave_up && (threadIdx.x & 31) == 0) {
+            *abort_flag = 1u;
+            atomicOr(&g_bfm_complete_err, 1u);
+        }
+        if (gave_up || __any_sync(~0u, *abort_flag != 0u)) {
+            bad = true;
+            return nullptr;
+        }
         return reinterpret_cast<const T*>(stages + slot * kStageBytes) + threadIdx.x;
     };
     auto release = [&]() {  // this warp is done with stage j
@@ -276,6 +288,7 @@ __global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2)
             uint32_t mw[G1];
             if constexpr (kStaged) {
                 const T* st = acquire();
+                if (!st) return;
 #pragma unroll
                 for (int u = 0; u < G1; ++u) raw[u] = (full || u < cnt) ? st[u * kThreads] : T(0);
             } else {
@@ -324,6 +337,7 @@ __global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2)
             T raw[G1];
             if constexpr (kStaged) {
                 const T* st = acquire();
+                if (!st) return;
 #pragma unroll
                 for (int u = 0; u < G1; ++u) raw[u] = (full || u < cnt) ? st[u * kThreads] : T(0);
             } else {
@@ -381,6 +395,7 @@ __global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2)
             if constexpr (kStaged) {
                 (void)old;
                 const T* st = acquire();
+                if (!st) return;
 #pragma unroll
                 for (int u = 0; u < G3; ++u) raw[u] = (full || u < cnt) ? st[u * kThreads] : T(0);
             } else {

@@ -53,6 +53,19 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(ptx::smem_u32(bar)) : "memory");
 }
 
+// The producer's wait for every consumer warp to release a slot: bounded by
+// limit_ns, and ended early by the CTA's abort flag (a consumer whose own wait
+// gave up raises it and never releases its stage).  False when it gave up.
+__device__ __forceinline__ bool wait_released(uint64_t* bar, uint32_t parity, volatile uint32_t* abort_flag,
+                                              uint64_t limit_ns) {
+    if (ptx::mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = ptx::globaltimer_ns();
+    while (true) {
+        if (ptx::mbar_try_wait_hint(bar, parity, 20000u)) return true;
+        if (*abort_flag || ptx::globaltimer_ns() - t0 > limit_ns) return false;
+    }
+}
+
 // y - x'beta (the residual of Eq. 3) with x a regressor row in shared memory.
 template <int K>
 __device__ __forceinline__ float residual(float y, const float* x, const float (&beta)[K]) {

@@ -28,6 +28,7 @@
 // residuals of a window alike.
 #include <cudaTypedefs.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -41,6 +42,13 @@
 namespace bfm {
 
 __device__ unsigned int g_bfm_stream_err = 0;  // bit 0: a stage wait gave up
+
+namespace {
+std::atomic<uint64_t> g_stage_wait_ns{2000000000ull};
+}
+
+uint64_t stage_wait_ns() { return g_stage_wait_ns.load(std::memory_order_relaxed); }
+void set_stage_wait_ns(uint64_t ns) { g_stage_wait_ns.store(ns ? ns : 2000000000ull, std::memory_order_relaxed); }
 
 cudaError_t stream_read_clear_errors(cudaStream_t s, unsigned int* bits) {
     unsigned int v = 0;
@@ -73,6 +81,7 @@ constexpr double kL2Budget = 80e6;           // bytes of history the resident pi
 constexpr uint64_t kWaitNs = 2000000000ull;  // bound of every wait
 
 struct StreamParams {
+    uint64_t wait_ns;  // bound of the consumers' stage waits (bfm_stage_wait_limit)
     const uint32_t* mask;
     int64_t m, mask_words;
     int N, n, hmax;
@@ -166,8 +175,9 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
             int64_t js = 0;
             for (; js < total; ++js) {
                 const int slot = (int)(js % kStages);
+                // the slot's previous stage released by every consumer warp
                 if (js >= kStages &&
-                    !ptx::mbar_wait_bounded(empty + slot, (uint32_t)(((js / kStages) - 1) & 1), kWaitNs)) {
+                    !wait_released(empty + slot, (uint32_t)(((js / kStages) - 1) & 1), abort_flag, kWaitNs)) {
                     *abort_flag = 1u;
                     atomicOr(&g_bfm_stream_err, 1u);
                     break;
@@ -194,10 +204,24 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
     // the consumers' stage j kept as (slot, lap parity): slot = j % kStages, phase = (j / kStages) & 1
     int cslot = 0;
     uint32_t cphase = 0;
-    auto acquire = [&]() -> const T* {  // wait for stage j; this thread's column in it
+    // Wait for stage j: this thread's column in it, or nullptr when the wait
+    // gave up or the CTA is aborting (warp-uniform).  A warp that gives up
+    // neither reads nor releases the stage, so the producer never refills a
+    // slot whose copy may still be in flight; it raises the abort flag at once.
+    auto acquire = [&]() -> const T* {
         const int slot = cslot;
-        const bool ok = ptx::mbar_wait_bounded(full + slot, cphase, kWaitNs);
-        if (__any_sync(~0u, !ok) || *abort_flag) bad = true;  // warp-uniform
+        // a bound below 1 us (a test of the failure path): one look at the barrier
+        const bool ok = P.wait_ns < 1000u ? ptx::mbar_test_wait(full + slot, cphase)
+                                          : ptx::mbar_wait_bounded(full + slot, cphase, P.wait_ns);
+        const bool gave_up = __any_sync(~0u, !ok);
+        if (gave_up && (threadIdx.x & 31) == 0) {
+            *abort_flag = 1u;
+            atomicOr(&g_bfm_stream_err, 1u);
+        }
+        if (gave_up || __any_sync(~0u, *abort_flag != 0u)) {
+            bad = true;
+            return nullptr;
+        }
         return reinterpret_cast<const T*>(stages + slot * kStageBytes) + threadIdx.x;
     };
     auto release = [&]() {  // this warp is done with stage j
@@ -248,6 +272,7 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
             constexpr bool full = decltype(full_c)::value;
             const int cnt = full ? G : n - d0;
             const T* st = acquire();
+            if (!st) return;
 #pragma unroll
             for (int u = 0; u < G; ++u) {
                 float y;
@@ -283,6 +308,7 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
             constexpr bool full = decltype(full_c)::value;
             const int cnt = full ? G : n - d0;
             const T* st = acquire();
+            if (!st) return;
 #pragma unroll
             for (int u = 0; u < G; ++u) {
                 float y;
@@ -331,6 +357,7 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
             constexpr bool full = decltype(full_c)::value;
             const int cnt = full ? G : n - d0;
             const T* st = acquire();
+            if (!st) return;
             if (__any_sync(~0u, q + G > 0)) {  // some pixel of the warp may reach its window in this batch
 #pragma unroll
                 for (int u = 0; u < G; ++u) {
@@ -364,6 +391,7 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
             constexpr bool full = decltype(full_c)::value;
             const int cnt = full ? G : N - d0;
             const T* st = acquire();
+            if (!st) return;
             // boundary test W^2 inv_scale^2 - b^2 > 0 (MO^2 > b^2): its maximum over
             // the batch, the first crossing searched only in a batch that has one
             float cv[G], blk = 0.f, cmax = -INFINITY;
@@ -503,6 +531,7 @@ bfm_status launch_stream(const bfm_design_s* d, int dtype, const void* Y, const 
     }
     const size_t elt = dtype == BFM_F32 ? 4 : 2;
     StreamParams P{};
+    P.wait_ns = stage_wait_ns();
     P.mask = mask;
     P.m = m;
     P.mask_words = (m + 31) / 32;
