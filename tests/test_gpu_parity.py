@@ -155,6 +155,43 @@ def test_host_entry_matches_device_entry(bfm):
         np.testing.assert_array_equal(out[key].numpy(), dev[key])
 
 
+@pytest.mark.parametrize("name,with_mask", [("c1", False), ("c3", False), ("c1", True)],
+                         ids=["float", "int16", "float-mask"])
+def test_host_entry_matches_oracle(bfm, name, with_mask):
+    """bfm_monitor_host from pinned host buffers (Y float or int16, optional
+    host mask bits) against the FP64 oracle element by element.  The chunk of
+    384 pixels holds one and a half 256-pixel kernel tiles, so chunk and tile
+    boundaries differ, and 3000 pixels leave a ragged last chunk of 312."""
+    m, chunk = 3000, 384
+    w = synth.workload(name, m=m)
+    Y = np.ascontiguousarray(w["Y"])
+    dtype = 1 if Y.dtype == np.int16 else 0
+    mask = None
+    if with_mask:
+        rng = np.random.default_rng(5)
+        mask = rng.integers(0, 2**32, size=(w["N"], (m + 31) // 32), dtype=np.uint64).astype(np.uint32)
+        mask |= rng.integers(0, 2**32, size=mask.shape, dtype=np.uint64).astype(np.uint32)   # ~75 % set
+    d = bfm.Design(w["dates"], w["k"], w["f"])
+    K = d.K
+    Yh = torch.from_numpy(Y).pin_memory()
+    mh = None if mask is None else torch.from_numpy(mask.view(np.int32)).pin_memory()
+    ws_bytes = bfm.bfm_monitor_host_workspace(d, dtype, chunk, with_mask)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    out = dict(break_idx=torch.empty(m, dtype=torch.int32).pin_memory(),
+               mean_mosum=torch.empty(m, dtype=torch.float32).pin_memory(),
+               sigma=torch.empty(m, dtype=torch.float32).pin_memory(),
+               beta=torch.empty((K, m), dtype=torch.float32).pin_memory(),
+               status=torch.empty(m, dtype=torch.uint8).pin_memory())
+    s = torch.cuda.current_stream()
+    bfm.bfm_monitor_host(d, Yh, dtype, mh, m, w["n_hist"], w["h_frac"], w["lam"], out["break_idx"],
+                         out["mean_mosum"], out["sigma"], out["beta"], out["status"], ws, ws_bytes, chunk, s)
+    s.synchronize()
+    assert bfm.bfm_device_errors() == 0
+    gpu = {k: v.numpy() for k, v in out.items()}
+    rep, ref = _check(w, Y, gpu, mask=mask)
+    assert (ref["break_idx"] >= 0).sum() > 300
+
+
 def test_invalid_arguments(bfm):
     w = synth.workload("c1", m=64)
     d = bfm.Design(w["dates"], 3, 23.0)
