@@ -296,9 +296,10 @@ def run_ours(args):
     def time_form(form):
         """Device-resident timing of one form: W warm-up calls, then K calls
         bracketed by CUDA events on the launching stream."""
-        if form in ("f32", "f32simt", "f32stream"):
+        if form in ("f32", "f32simt", "f32stream", "f32hybrid"):
             Yf, dt = Y, bfm.BFM_F32
-            algo = {"f32": bfm.BFM_ALGO_MMA, "f32simt": bfm.BFM_ALGO_SIMT, "f32stream": bfm.BFM_ALGO_STREAM}[form]
+            algo = {"f32": bfm.BFM_ALGO_MMA, "f32simt": bfm.BFM_ALGO_SIMT, "f32stream": bfm.BFM_ALGO_STREAM,
+                    "f32hybrid": bfm.BFM_ALGO_HYBRID}[form]
         elif form == "f32complete":
             # the same scene recipe without clouds: the shared pseudo-inverse form
             Yf = synth.workload_torch("c2_complete", device=dev, dtype="f32", m=args.pixels)["Y"]
@@ -306,7 +307,8 @@ def run_ours(args):
         else:
             Yf = torch.where(torch.isnan(Y), torch.full_like(Y, -32768.0),
                              torch.clamp(torch.round(Y * 1e4), -32767, 32767)).to(torch.int16)
-            dt, algo = bfm.BFM_I16, (bfm.BFM_ALGO_STREAM if form == "i16stream" else bfm.BFM_ALGO_MMA)
+            dt = bfm.BFM_I16
+            algo = {"i16stream": bfm.BFM_ALGO_STREAM, "i16hybrid": bfm.BFM_ALGO_HYBRID}.get(form, bfm.BFM_ALGO_MMA)
 
         def step():
             bfm.bfm_monitor_ex(design, Yf, dt, None, m, n_hist, w["h_frac"], w["lam"], out["break_idx"],
@@ -350,6 +352,8 @@ def run_ours(args):
                 "clocks": clk, "dtype": "i16" if form.startswith("i16") else "f32",
                 "algo": {"f32simt": "simt", "f32stream": "stream (CUDA cores, TMA stages)",
                          "i16stream": "stream (CUDA cores, TMA stages)",
+                         "f32hybrid": "hybrid (tcgen05 contractions, CUDA-core scans, TMA stages)",
+                         "i16hybrid": "hybrid (tcgen05 contractions, CUDA-core scans, TMA stages)",
                          "f32complete": "complete-series (shared pseudo-inverse)"}.get(form, "tcgen05")}
 
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]

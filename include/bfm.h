@@ -94,13 +94,26 @@ enum {
  * window from a per-thread ring of the last h_p residuals.  Needs Y with a
  * 16-byte aligned base and rows of a multiple of 16 bytes, and the basis
  * tables plus floor(h_frac * n_hist) ring slots per pixel within 112 KB of
+ * shared memory (else BFM_EUNSUPPORTED).
+ * BFM_ALGO_HYBRID: the streaming scan with every contraction over dates on
+ * the tensor cores (tcgen05, accumulators and A operands in tensor memory):
+ * the masked basis sums (fp16 basis hi + lo) and X'My (tf32) per 16-date
+ * chunk, the fitted values of beta0 and of beta0 + delta (fp16 hi + lo
+ * coefficients and regressors) per 32-date piece, and the refinement sums
+ * X'M r0 (fp16 hi + lo residuals).  512 pixels per CTA, one CTA per SM, three
+ * passes over each pixel's column (history twice, then the dates from the
+ * earliest first-window observation of the tile on).  Same outputs and
+ * conventions as BFM_ALGO_STREAM.  Needs Y with a 16-byte aligned base and
+ * rows of a multiple of 16 bytes, and the tables, three 16 KB stages and a
+ * ring of floor(h_frac * n_hist) residuals for 512 pixels within one SM's
  * shared memory (else BFM_EUNSUPPORTED). */
 typedef enum {
     BFM_ALGO_AUTO = 0,
     BFM_ALGO_SIMT = 1, /* FP32 CUDA-core path ("plain form") */
     BFM_ALGO_MMA = 2,  /* tensor-core normal equations, fitted values and refinement */
     BFM_ALGO_COMPLETE = 3, /* series without missing values: one shared pseudo-inverse */
-    BFM_ALGO_STREAM = 4    /* one CUDA-core thread per pixel, Y streamed through TMA stages */
+    BFM_ALGO_STREAM = 4,   /* one CUDA-core thread per pixel, Y streamed through TMA stages */
+    BFM_ALGO_HYBRID = 5    /* as STREAM, with every contraction over dates on the tensor cores */
 } bfm_algo;
 
 typedef struct bfm_design_s *bfm_design_t;
@@ -442,8 +455,8 @@ bfm_status bfm_device_errors(void *stream, uint32_t *bits);
 
 /*
  * bfm_stage_wait_limit -- the bound, in nanoseconds, of the waits in which
- * the streaming form's (BFM_ALGO_STREAM) pixel warps wait for a stage of Y to
- * land in shared memory.  The paper has no counterpart: every wait of the
+ * the pixel warps of the streaming and hybrid forms (BFM_ALGO_STREAM,
+ * BFM_ALGO_HYBRID) wait for a stage of Y to land in shared memory.  The paper has no counterpart: every wait of the
  * library is bounded so that a stalled copy ends the kernel with an error
  * instead of hanging the GPU, and this setter lets a test make such a wait run
  * out.  A wait that runs out stops its warp: the warp's pixels from that tile

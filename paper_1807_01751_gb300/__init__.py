@@ -22,7 +22,7 @@ import threading
 from . import _build
 
 BFM_F32, BFM_I16 = 0, 1
-BFM_ALGO_AUTO, BFM_ALGO_SIMT, BFM_ALGO_MMA, BFM_ALGO_COMPLETE, BFM_ALGO_STREAM = 0, 1, 2, 3, 4
+BFM_ALGO_AUTO, BFM_ALGO_SIMT, BFM_ALGO_MMA, BFM_ALGO_COMPLETE, BFM_ALGO_STREAM, BFM_ALGO_HYBRID = 0, 1, 2, 3, 4, 5
 BFM_PX_INCOMPLETE = 5
 STATUS_NAMES = {0: "OK", 1: "INSUFFICIENT_HISTORY", 2: "SINGULAR", 3: "DEGENERATE", 4: "NO_MONITOR", 5: "INCOMPLETE",
                 255: "TIMEOUT"}

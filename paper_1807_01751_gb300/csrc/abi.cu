@@ -278,12 +278,19 @@ bfm_status bfm_design_create(const double* dates, int N, int k_harm, double f, b
         d->npad_tc = npad;
     }
     if (e == cudaSuccess) {
+        std::vector<unsigned char> tab;
+        hybrid_tables(*d, rowsd, tab);
+        e = cudaMalloc(&d->d_hyb, tab.size());
+        if (e == cudaSuccess) e = cudaMemcpy(d->d_hyb, tab.data(), tab.size(), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) {
         e = cudaMalloc(&d->d_dates, sizeof(double) * (size_t)N);
         if (e == cudaSuccess) e = cudaMemcpy(d->d_dates, dates, sizeof(double) * (size_t)N, cudaMemcpyHostToDevice);
     }
     if (e != cudaSuccess) {
         cudaFree(d->d_basis);
         if (d->d_phi_tc) cudaFree(d->d_phi_tc);
+        if (d->d_hyb) cudaFree(d->d_hyb);
         if (d->d_dates) cudaFree(d->d_dates);
         delete d;
         return cuda_fail(e, "bfm_design_create: device tables");
@@ -308,6 +315,7 @@ bfm_status bfm_design_destroy(bfm_design_t d) {
                 if (cur != d->device) cudaSetDevice(d->device);
                 cudaFree(d->d_basis);
                 if (d->d_phi_tc) cudaFree(d->d_phi_tc);
+                if (d->d_hyb) cudaFree(d->d_hyb);
                 if (d->d_dates) cudaFree(d->d_dates);
                 for (auto& c : d->complete) cudaFree(c.d_tab);
                 if (cur != d->device) cudaSetDevice(cur);
@@ -349,10 +357,13 @@ bfm_status bfm_monitor_ext(bfm_design_t d, const void* Y, int dtype, const uint3
         return BFM_EINVAL;
     }
     if (algo != BFM_ALGO_AUTO && algo != BFM_ALGO_SIMT && algo != BFM_ALGO_MMA && algo != BFM_ALGO_COMPLETE &&
-        algo != BFM_ALGO_STREAM) {
+        algo != BFM_ALGO_STREAM && algo != BFM_ALGO_HYBRID) {
         set_error("bfm_monitor: unknown algo");
         return BFM_EINVAL;
     }
+    if (algo == BFM_ALGO_HYBRID)
+        return launch_hybrid(d, dtype, Y, mask_bits, m, n_hist, h_frac, lambda, break_idx, mean_mosum, sigma, beta,
+                             status, (cudaStream_t)stream, max_mosum);
     if (algo == BFM_ALGO_STREAM)
         return launch_stream(d, dtype, Y, mask_bits, m, n_hist, h_frac, lambda, break_idx, mean_mosum, sigma, beta,
                              status, (cudaStream_t)stream, max_mosum);
@@ -503,13 +514,14 @@ bfm_status bfm_device_errors(void* stream, uint32_t* bits) {
         set_error("bfm_device_errors: bits is NULL");
         return BFM_EINVAL;
     }
-    unsigned int v = 0, v2 = 0, v3 = 0, v4 = 0;
+    unsigned int v = 0, v2 = 0, v3 = 0, v4 = 0, v5 = 0;
     cudaError_t e = simt_read_clear_errors((cudaStream_t)stream, &v);
     if (e == cudaSuccess) e = mma_read_clear_errors((cudaStream_t)stream, &v2);
     if (e == cudaSuccess) e = complete_read_clear_errors((cudaStream_t)stream, &v3);
     if (e == cudaSuccess) e = stream_read_clear_errors((cudaStream_t)stream, &v4);
+    if (e == cudaSuccess) e = hybrid_read_clear_errors((cudaStream_t)stream, &v5);
     if (e != cudaSuccess) return cuda_fail(e, "bfm_device_errors");
-    v |= v2 | v3 | v4;
+    v |= v2 | v3 | v4 | v5;
     *bits = v;
     return BFM_OK;
 }

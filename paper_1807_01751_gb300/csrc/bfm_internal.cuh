@@ -154,6 +154,9 @@ struct bfm_design_s {
     // exceeds the tensor-core limit.
     void* d_phi_tc = nullptr;
     int npad_tc = 0;
+    // Hybrid-form tables (hybrid.cu hybrid_tables): Gram hi/lo, tf32 regressors,
+    // fitted-value regressors hi/lo.
+    void* d_hyb = nullptr;
     int device = -1;
     int refcount = 0;
     uint64_t key = 0;
@@ -190,6 +193,14 @@ bfm_status launch_stream(const bfm_design_s* d, int dtype, const void* Y, const 
                          int n_hist, double h_frac, double lambda, int32_t* brk, float* mean, float* sigma,
                          float* beta, uint8_t* status, cudaStream_t stream, float* maxmo);
 cudaError_t stream_read_clear_errors(cudaStream_t s, unsigned int* bits);
+// Hybrid form (hybrid.cu): tensor-core contractions, one thread per pixel for the scans.
+void hybrid_tables(const bfm_design_s& d, const std::vector<double>& rows, std::vector<unsigned char>& out);
+bool hybrid_supported(const bfm_design_s* d, int dtype, int n_hist, double h_frac, const void* Y, int64_t m);
+bfm_status launch_hybrid(const bfm_design_s* d, int dtype, const void* Y, const uint32_t* mask, int64_t m,
+                         int n_hist, double h_frac, double lambda, int32_t* brk, float* mean, float* sigma,
+                         float* beta, uint8_t* status, cudaStream_t stream, float* maxmo);
+cudaError_t hybrid_read_clear_errors(cudaStream_t s, unsigned int* bits);
+
 // Bound of the staged forms' consumer-side stage waits (bfm_stage_wait_limit).
 uint64_t stage_wait_ns();
 void set_stage_wait_ns(uint64_t ns);

@@ -2,7 +2,7 @@
 
 Every wait of the library's kernels is bounded, so that a copy that never
 lands ends the kernel with an error status instead of hanging the GPU.  Here
-the streaming form's consumer-side stage wait is shortened (bfm_stage_wait_limit)
+the consumer-side stage wait of the staged forms is shortened (bfm_stage_wait_limit)
 until it gives up at the first stage that has not landed yet: the kernel must
 end, set bit 0 of the device error word, mark the unfinished pixels
 BFM_PX_TIMEOUT with the unfitted outputs, and leave the context usable, so
@@ -19,7 +19,7 @@ import oracle
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-STREAM = 4
+STREAM, HYBRID = 4, 5
 TIMEOUT = 255
 
 
@@ -32,12 +32,13 @@ def bfm():
     return bfm
 
 
+@pytest.mark.parametrize("algo", [STREAM, HYBRID], ids=["stream", "hybrid"])
 @pytest.mark.parametrize("name", ["c1", "c3"])
-def test_stage_wait_runs_out_then_recovers(bfm, name):
+def test_stage_wait_runs_out_then_recovers(bfm, name, algo):
     w = synth.workload(name, m=4096)
     d = bfm.Design(w["dates"], w["k"], w["f"])
     Yd = torch.from_numpy(np.ascontiguousarray(w["Y"])).cuda()
-    kw = dict(n_hist=w["n_hist"], h_frac=w["h_frac"], lam=w["lam"], algo=STREAM)
+    kw = dict(n_hist=w["n_hist"], h_frac=w["h_frac"], lam=w["lam"], algo=algo)
     assert bfm.bfm_device_errors() == 0
     bfm.bfm_stage_wait_limit(1)          # one look at each stage barrier, no waiting
     try:
