@@ -38,9 +38,10 @@ sys.path.insert(0, ROOT)
 METRIC = "BFAST-monitor pixels/s at 8.4M px x 414 dates; p50/p99 tile latency"
 # DRAM bytes per pixel per launch from the ncu captures summarised in
 # profiles/ (None once the kernel changes after the capture).
-TRAFFIC_PER_PX = {"f32": (1.7866e9 / 1048576,), "f32simt": (None,), "f32stream": (1.8983e9 / 1048576,),
-                  "i16": (None,),
+TRAFFIC_PER_PX = {"f32": (1.7866e9 / 1048576,), "f32simt": (None,), "f32stream": (None,),
+                  "i16": (None,), "f32hybrid": (None,), "i16hybrid": (None,),
                   "i16stream": (None,), "f32complete": (1.7958e9 / 1048576,)}
+SAMPLE_PX = 4096  # pixels of each timed form checked against the oracle (outside the timed region)
 
 WORKLOAD = "c2: full scene 8,388,608 px x 414 dates, n_hist=228, K=8, f=23, h=0.25, plain float32"
 
@@ -143,6 +144,74 @@ def cpu_oracle_rate(Y_host, dates, k, f, n_hist, h_frac, lam, budget_s: float):
         n += cols.shape[1]
         c0 += blk
     return n / dt, n, dt
+
+
+def cpu_oracle_one_core(Y_host, dates, n_hist, h_frac, lam):
+    """The oracle on one host core (OMP_NUM_THREADS=1 in a child process) on
+    the first 16,384 pixels of the scene."""
+    cols = np.ascontiguousarray(Y_host[:, :16384].numpy())
+    with tempfile.TemporaryDirectory() as td:
+        np.save(os.path.join(td, "y.npy"), cols)
+        np.save(os.path.join(td, "d.npy"), np.asarray(dates))
+        code = ("import sys, time, numpy as np; sys.path.insert(0, %r); import oracle; "
+                "y = np.load(%r); d = np.load(%r); t0 = time.perf_counter(); "
+                "oracle.monitor(d, y, k=3, f=23.0, n_hist=%d, h_frac=%r, lam=%r); "
+                "print(y.shape[1] / (time.perf_counter() - t0))"
+                % (ROOT, os.path.join(td, "y.npy"), os.path.join(td, "d.npy"), n_hist, h_frac, lam))
+        env = dict(os.environ, OMP_NUM_THREADS="1")
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    try:
+        v = float(r.stdout.strip().splitlines()[-1])
+    except (ValueError, IndexError):
+        return {"value": None, "error": r.stderr[-300:]}
+    return {"value": v, "unit": "pixels/s", "cores": 1, "sample": "first 16384 pixels of the same scene"}
+
+
+def cpu_oracle_c1():
+    """The oracle on all host cores on the c1 scene (4096 pixels x 228 dates)."""
+    import oracle
+    import synth
+    w1 = synth.workload("c1")
+    t0 = time.perf_counter()
+    oracle.monitor(w1["dates"], w1["Y"], k=3, f=23.0, n_hist=w1["n_hist"], h_frac=w1["h_frac"], lam=w1["lam"])
+    dt = time.perf_counter() - t0
+    return {"value": w1["m"] / dt, "unit": "pixels/s", "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count())),
+            "workload": "c1: 4096 pixels x 228 dates, n_hist 100, K 8, 30 % i.i.d. missing"}
+
+
+def oracle_on(Y, dates, n_hist, h_frac, lam):
+    import oracle
+    return oracle.monitor(dates, np.ascontiguousarray(Y), k=3, f=23.0, n_hist=n_hist, h_frac=h_frac, lam=lam)
+
+
+def form_errors(gpu: dict, ref: dict, dates) -> dict:
+    """Each output's error against the FP64 oracle on the sample: beta in the
+    column-scaled norm (max_i |dbeta_i| ||X_i||inf / max_i |beta_i| ||X_i||inf),
+    sigma-hat relative, mean MOSUM |d| / max(1, |ref|), status mismatches, and
+    break mismatches on pixels whose boundary margin is >= 1e-5 (untied) and
+    below it (margin-tied, counted)."""
+    import oracle
+    st_g, st_r = gpu["status"], ref["status"]
+    same = st_g == st_r
+    tie = ref["margin"] < 1e-5
+    bmis = (gpu["break_idx"] != ref["break_idx"]) & same
+    X = oracle.design(dates, 3, 23.0)
+    colmax = np.abs(X).max(axis=0)[:, None]
+    fitted = same & np.isin(st_r, [0, 3, 4])
+    be = 0.0
+    if fitted.any():
+        num = np.max(np.abs(gpu["beta"].astype(np.float64)[:, fitted] - ref["beta"][:, fitted]) * colmax, axis=0)
+        den = np.max(np.abs(ref["beta"][:, fitted]) * colmax, axis=0)
+        be = float((num / np.maximum(den, 1e-300)).max())
+    so = same & np.isin(st_r, [0, 4])
+    se = float((np.abs(gpu["sigma"].astype(np.float64)[so] - ref["sigma"][so]) / ref["sigma"][so]).max()) if so.any() else 0.0
+    mo = same & (st_r == 0)
+    me = float((np.abs(gpu["mean_mosum"].astype(np.float64)[mo] - ref["mean_mosum"][mo])
+                / np.maximum(1.0, np.abs(ref["mean_mosum"][mo]))).max()) if mo.any() else 0.0
+    return {"pixels": int(st_r.size), "beta_col_scaled_max": be, "sigma_rel_max": se, "mean_mosum_max": me,
+            "status_mismatch": int((~same).sum()), "break_mismatch_untied": int((bmis & ~tie).sum()),
+            "break_mismatch_tied": int((bmis & tie).sum()), "margin_tied": int(tie.sum()),
+            "breaks": int((ref["break_idx"] >= 0).sum())}
 
 
 def run_reference(args):
@@ -252,7 +321,7 @@ def run_tiles_and_serving(bfm, synth, torch, dev, stream):
     for rate in (10, 20, 50, 100, 200, 500):
         n_req = min(1000, max(50, 2 * rate))
         arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
-        srv = bfm.Server(hbm_budget=32 << 30, slots=4)
+        srv = bfm.Server(hbm_budget=150 << 30, slots=4)
         tickets = []
         t0 = time.perf_counter()
         for i, a in enumerate(arrivals):
@@ -336,6 +405,10 @@ def run_ours(args):
         clk = clocks.stop()
         per = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
         total_ms = slowest_rank(evs[0].elapsed_time(evs[-1]), dev)
+        # outputs and input columns of the seeded sample, for the error statement (after timing)
+        samples[form] = dict(out={k: (v[:, sidx] if v.dim() == 2 else v[sidx]).cpu().numpy() for k, v in out.items()},
+                             Y=Yf[:, sidx].cpu().numpy(), scene="complete" if form == "f32complete" else
+                             ("i16" if form.startswith("i16") else "f32"))
         elt = 2 if form.startswith("i16") else 4
         alg_bytes = N * m * elt + m * (4 + 4 + 4 + 4 * K + 1)
         achieved = alg_bytes / (statistics.mean(per) / 1e3) / 1e9
@@ -357,43 +430,71 @@ def run_ours(args):
                          "f32complete": "complete-series (shared pseudo-inverse)"}.get(form, "tcgen05")}
 
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
+    samples = {}
+    sidx = torch.from_numpy(np.unique(np.concatenate([
+        np.arange(64), np.arange(m - 64, m),
+        np.random.default_rng(0).choice(m, SAMPLE_PX - 128, replace=False)]))).to(dev)
     res = {f: time_form(f) for f in forms}
     form = forms[0]
     main = res[form]
     value, ms_step = main["value"], main["ms_per_step"]
     elt = 2 if form.startswith("i16") else 4
 
-    # ---- end to end (float32 scene through bfm_monitor_host) through the host-buffer entry point ------------------------------
-    e2e = None
+    # ---- end to end through the host-buffer entry point (pinned host Y and outputs): float32,
+    # and the same scene stored as int16 (half the bytes over the host link)
+    e2e = e2e_i16 = link = None
     if not args.no_e2e:
         Yh = torch.empty(Y.shape, dtype=Y.dtype, pin_memory=True)
         Yh.copy_(Y)
-        e_dt, e_elt = bfm.BFM_F32, 4
+        Yh16 = torch.empty(Y.shape, dtype=torch.int16, pin_memory=True)
+        Yh16.copy_(torch.where(torch.isnan(Y), torch.full_like(Y, -32768.0),
+                               torch.clamp(torch.round(Y * 1e4), -32767, 32767)).to(torch.int16))
         oh = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()}
         chunk = 1 << 20
-        wsb = bfm.bfm_monitor_host_workspace(design, e_dt, chunk, False)
-        wbuf = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        wsb = max(bfm.bfm_monitor_host_workspace(design, bfm.BFM_F32, chunk, False),
+                  bfm.bfm_monitor_host_workspace(design, bfm.BFM_I16, chunk, False))
         del Y
         torch.cuda.empty_cache()
-
-        def hstep():
-            bfm.bfm_monitor_host(design, Yh, e_dt, None, m, n_hist, w["h_frac"], w["lam"], oh["break_idx"],
-                                 oh["mean_mosum"], oh["sigma"], oh["beta"], oh["status"], wbuf, wsb, chunk, stream)
-
-        hstep()
+        wbuf = torch.empty(wsb, dtype=torch.uint8, device=dev)
+        # the host link itself: one pinned 1 GiB host-to-device copy
+        lb = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
+        lh = Yh.view(torch.uint8).reshape(-1)[:1 << 30]
+        lb.copy_(lh, non_blocking=True)
         torch.cuda.synchronize()
-        e_steps = max(2, min(args.steps, 10))
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(e_steps):
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        for _ in range(3):
+            lb.copy_(lh, non_blocking=True)
+        l1.record(stream)
+        torch.cuda.synchronize()
+        link = {"h2d_gbs": 3 * (1 << 30) / (l0.elapsed_time(l1) / 1e3) / 1e9,
+                "how": "pinned host 1 GiB -> device, torch copy, 3 copies timed with CUDA events"}
+        del lb
+
+        def host_leg(Yhost, e_dt, e_elt):
+            def hstep():
+                bfm.bfm_monitor_host(design, Yhost, e_dt, None, m, n_hist, w["h_frac"], w["lam"], oh["break_idx"],
+                                     oh["mean_mosum"], oh["sigma"], oh["beta"], oh["status"], wbuf, wsb, chunk, stream)
+
             hstep()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        e_ms = slowest_rank(e0.elapsed_time(e1) / e_steps, dev)
-        e2e = {"value": job_rate(m, 1, ws, e_ms), "unit": "pixels/s", "h2d_bytes_per_step": N * m * e_elt,
-               "d2h_bytes_per_step": m * (4 + 4 + 4 + 4 * K + 1), "ms_per_step": e_ms,
-               "api": "bfm_monitor_host (pinned host Y and outputs, 1 Mi-pixel chunks)"}
+            torch.cuda.synchronize()
+            e_steps = max(2, min(args.steps, 10))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(e_steps):
+                hstep()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            e_ms = slowest_rank(e0.elapsed_time(e1) / e_steps, dev)
+            return {"value": job_rate(m, 1, ws, e_ms), "unit": "pixels/s", "h2d_bytes_per_step": N * m * e_elt,
+                    "d2h_bytes_per_step": m * (4 + 4 + 4 + 4 * K + 1), "ms_per_step": e_ms,
+                    "api": "bfm_monitor_host (pinned host Y and outputs, 1 Mi-pixel chunks, form AUTO picks)",
+                    "dtype": "f32" if e_elt == 4 else "i16"}
+
+        e2e = host_leg(Yh, bfm.BFM_F32, 4)
+        e2e_i16 = host_leg(Yh16, bfm.BFM_I16, 2)
+        del Yh16
         Ysrc = Yh
     else:
         Ysrc = Y[:, :1 << 20].cpu()
@@ -403,6 +504,14 @@ def run_ours(args):
         rate, n, dt = cpu_oracle_rate(Ysrc, w["dates"], 3, 23.0, n_hist, w["h_frac"], w["lam"], budget_s=15.0)
         cpu = {"value": rate, "unit": "pixels/s", "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count())),
                "kind": "oracle", "sample": f"first {n} pixels of the same scene, all {N} dates, FP64 oracle ({dt:.1f} s)"}
+        cpu["one_core"] = cpu_oracle_one_core(Ysrc, w["dates"], n_hist, w["h_frac"], w["lam"])
+        cpu["c1"] = cpu_oracle_c1()
+        # the same oracle on the seeded sample of every timed form: each output's error against FP64
+        ref_cache = {}
+        for f, smp in samples.items():
+            if smp["scene"] not in ref_cache:
+                ref_cache[smp["scene"]] = oracle_on(smp["Y"], w["dates"], n_hist, w["h_frac"], w["lam"])
+            res[f]["errors_vs_oracle"] = form_errors(smp["out"], ref_cache[smp["scene"]], w["dates"])
 
     # critical value of Eq. 4 by simulation (c2's alpha, h and N/n): 1e5 paths, 1000 steps per unit
     lam_sim = None
@@ -413,6 +522,13 @@ def run_ours(args):
         lam_sim = {"alpha": 0.05, "h": 0.25, "T": N / n_hist, "grid_per_unit": 1000, "paths": 100000,
                    "lambda": lam_v, "ms": lam_ms, "paths_per_s": 1e5 / (lam_ms / 1e3),
                    "note": "bfm_lambda, one FP64 path per thread, host quantile; wall time of the call"}
+
+    # the per-pixel solve of Eq. 6 (two per pixel) in FP64 and in FP32, for every pixel of the scene
+    solve = None
+    if rank == 0:
+        solve = {"systems": m, "K": K, "fp64_ms": bfm.bfm_solve_rate(K, m, True, stream),
+                 "fp32_ms": bfm.bfm_solve_rate(K, m, False, stream),
+                 "note": "bfm_solve_rate: Cholesky + two triangular solves, twice per system, CUDA events"}
 
     c4 = c5 = None
     if not args.no_c4c5:
@@ -431,9 +547,11 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (Y is %.1f GB per step)" % (N * m * elt / 1e9),
                    "parallelism": f"{ws} independent scene(s), one per GPU"},
         "latency_ms": main["latency_ms"], "roofline": main["roofline"],
-        "cpu_baseline": cpu, "e2e": e2e, "clocks": main["clocks"], "gpu_launches": args.steps,
+        "cpu_baseline": cpu, "e2e": e2e, "e2e_int16": e2e_i16, "host_link": link, "clocks": main["clocks"],
+        "gpu_launches": args.steps,
         "forms": {f: {k: v for k, v in r.items() if k != "clocks"} for f, r in res.items()},
-        "c4": c4, "c5": c5, "lambda_simulation": lam_sim,
+        "c4": c4, "c5": c5, "lambda_simulation": lam_sim, "solve_fp64_vs_fp32": solve,
+        "errors_vs_oracle": main.get("errors_vs_oracle"),
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -448,10 +566,11 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--forms", default="f32stream,f32,f32simt,i16stream,i16,f32complete",
-                    help="comma list; the first is the headline (f32stream = float storage, one CUDA-core "
-                         "thread per pixel streamed through TMA stages (the form AUTO takes), f32 = float "
-                         "storage on tensor cores, i16stream = int16 storage in the streaming form, "
+    ap.add_argument("--forms", default="f32hybrid,f32stream,f32,f32simt,i16hybrid,i16stream,i16,f32complete",
+                    help="comma list; the first is the headline (f32hybrid = float storage, tensor-core "
+                         "contractions with one CUDA-core thread per pixel for the scans (the form AUTO takes), "
+                         "f32stream = float storage, the streaming CUDA-core form, f32 = float "
+                         "storage on tensor cores, i16hybrid / i16stream = int16 storage in those forms, "
                          "f32simt = float storage on CUDA cores, i16 = int16 storage on tensor cores, "
                          "f32complete = the same scene without clouds in the shared pseudo-inverse form)")
     ap.add_argument("--no-e2e", action="store_true")

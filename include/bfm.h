@@ -64,9 +64,9 @@ enum {
     BFM_PX_TIMEOUT = 255             /* the tile's load wait gave up (device error) */
 };
 
-/* Algorithm variants for bfm_monitor_ex.  BFM_ALGO_AUTO takes the
- * streaming form (BFM_ALGO_STREAM, below) where it applies, else the
- * tensor-core form where it applies -- its shared memory (basis tables over
+/* Algorithm variants for bfm_monitor_ex.  BFM_ALGO_AUTO takes the hybrid
+ * form (BFM_ALGO_HYBRID, below) where it applies, else the streaming form
+ * (BFM_ALGO_STREAM) where it applies, else the tensor-core form where it applies -- its shared memory (basis tables over
  * the N dates, a MOSUM ring of floor(h_frac * n_hist) + 17 prefix sums per
  * pixel, the Y stages) fits one SM, and Y can be described by a tensor map
  * (16-byte aligned base, m >= 128, rows a multiple of 16 bytes) -- else the
@@ -263,8 +263,8 @@ bfm_status bfm_trace(bfm_design_t d, const void *Y, int dtype, const uint32_t *m
                      double h_frac, const int64_t *pixels, int64_t count, const uint8_t *status, float *mo,
                      float *resid, void *stream);
 
-/* The form BFM_ALGO_AUTO takes for these arguments (BFM_ALGO_SIMT or
- * BFM_ALGO_MMA; no work, no device access).  Y and m matter only through
+/* The form BFM_ALGO_AUTO takes for these arguments (BFM_ALGO_HYBRID,
+ * BFM_ALGO_STREAM, BFM_ALGO_MMA or BFM_ALGO_SIMT; no work, no device access).  Y and m matter only through
  * Y's alignment and m; a NULL or invalid design gives BFM_ALGO_SIMT. */
 int bfm_algo_auto(bfm_design_t d, int dtype, int n_hist, double h_frac, const void *Y, int64_t m);
 
@@ -448,6 +448,18 @@ typedef struct {
     uint8_t *status;
 } bfm_tile_spec;
 bfm_status bfm_batch_run_static(const bfm_tile_spec *tiles, int ntiles, void *stream);
+
+/*
+ * bfm_solve_rate -- measured device time of the per-pixel K x K solve of
+ * Eq. 6 (Cholesky factor, forward and backward substitution) done twice per
+ * system (as for beta0 and for the refinement delta), for `systems` synthetic
+ * symmetric positive definite systems, in FP64 (fp64 != 0) or FP32.  A
+ * diagnostic: it is the figure behind running the solves in FP32 with one
+ * refinement step.  *ms_out receives the time of the solves alone (the same
+ * launch without them subtracted).  K is 4, 6 or 8; 1 <= systems <= 2^31.
+ * Synchronises `stream`.  BFM_EINVAL on bad arguments.
+ */
+bfm_status bfm_solve_rate(int K, int64_t systems, int fp64, void *stream, float *ms_out);
 
 /* Reads and clears the library's device error word (bit 0: a tile load wait
  * gave up).  Synchronises `stream`. */

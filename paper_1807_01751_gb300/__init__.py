@@ -111,6 +111,8 @@ def load(build_if_missing: bool = True):
         lib.bfm_device_errors.restype = i32
         lib.bfm_stage_wait_limit.argtypes = [ctypes.c_uint64]
         lib.bfm_stage_wait_limit.restype = i32
+        lib.bfm_solve_rate.argtypes = [i32, i64, i32, vp, ctypes.POINTER(ctypes.c_float)]
+        lib.bfm_solve_rate.restype = i32
         lib.bfm_batch_create.argtypes = [ctypes.POINTER(vp)]
         lib.bfm_batch_create.restype = i32
         lib.bfm_batch_add.argtypes = [vp, vp, vp, i32, vp, i64, i32, dbl, dbl, vp, vp, vp, vp, vp,
@@ -264,6 +266,13 @@ def bfm_device_errors(stream=None) -> int:
     v = ctypes.c_uint32(0)
     _check(load().bfm_device_errors(_stream(stream), ctypes.byref(v)))
     return v.value
+
+
+def bfm_solve_rate(K: int, systems: int, fp64: bool, stream=None) -> float:
+    """Device ms of two K x K Cholesky solves per system for `systems` systems (FP64 or FP32)."""
+    ms = ctypes.c_float(0.0)
+    _check(load().bfm_solve_rate(int(K), int(systems), 1 if fp64 else 0, _stream(stream), ctypes.byref(ms)))
+    return ms.value
 
 
 def bfm_stage_wait_limit(consumer_wait_ns: int) -> None:

@@ -185,6 +185,7 @@ bfm_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 int auto_form(const bfm_design_s* d, int dtype, int n_hist, double h_frac, const void* Y, int64_t m) {
+    if (hybrid_supported(d, dtype, n_hist, h_frac, Y, m)) return BFM_ALGO_HYBRID;
     if (stream_supported(d, dtype, n_hist, h_frac, Y, m)) return BFM_ALGO_STREAM;
     if (mma_supported(d, dtype, n_hist, h_frac, Y, m, nullptr)) return BFM_ALGO_MMA;
     return BFM_ALGO_SIMT;
@@ -375,6 +376,9 @@ bfm_status bfm_monitor_ext(bfm_design_t d, const void* Y, int dtype, const uint3
         set_error("bfm_monitor: the tensor-core form needs basis tables and a MOSUM ring (bandwidth + 17 prefix sums per pixel) that fits shared memory, and Y with a 16-byte aligned base, m >= 128 and rows of a multiple of 16 bytes");
         return BFM_EUNSUPPORTED;
     }
+    if (algo == BFM_ALGO_AUTO && hybrid_supported(d, dtype, n_hist, h_frac, Y, m))
+        return launch_hybrid(d, dtype, Y, mask_bits, m, n_hist, h_frac, lambda, break_idx, mean_mosum, sigma, beta,
+                             status, (cudaStream_t)stream, max_mosum);
     if (algo == BFM_ALGO_AUTO && stream_supported(d, dtype, n_hist, h_frac, Y, m))
         return launch_stream(d, dtype, Y, mask_bits, m, n_hist, h_frac, lambda, break_idx, mean_mosum, sigma, beta,
                              status, (cudaStream_t)stream, max_mosum);
@@ -474,7 +478,10 @@ bfm_status bfm_monitor_host(bfm_design_t d, const void* Y_host, int dtype, const
             float* obeta = reinterpret_cast<float*>(base + L.beta);
             uint8_t* ost = reinterpret_cast<uint8_t*>(base + L.status);
             const int form = auto_form(d, dtype, n_hist, h_frac, base + L.y, mc);
-            st = form == BFM_ALGO_STREAM
+            st = form == BFM_ALGO_HYBRID
+                     ? launch_hybrid(d, dtype, base + L.y, mk, mc, n_hist, h_frac, lambda, ob, om, os, obeta, ost, cs,
+                                     nullptr)
+                 : form == BFM_ALGO_STREAM
                      ? launch_stream(d, dtype, base + L.y, mk, mc, n_hist, h_frac, lambda, ob, om, os, obeta, ost, cs,
                                      nullptr)
                  : form == BFM_ALGO_MMA

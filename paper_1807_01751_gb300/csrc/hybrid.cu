@@ -92,10 +92,15 @@ constexpr size_t kSmemCap = 232448;       // opt-in dynamic shared memory per bl
 
 // TMEM columns within an M-tile's 128 (the phases reuse them in turn):
 //   pass A : G sums [0, 32), X'My [32, 48), A buffers 2 x (mask 8 | y 16) [48, 96)
-//   pass B': c [0, 16), beta0 coefficients [16, 32), r0 buffers 2 x (hi 8 | lo 8) [32, 64),
-//            fitted-value pieces 2 x 32 [64, 128)
-//   pass C : delta coefficients [0, 16), beta0 coefficients [16, 32), pieces [64, 128)
-constexpr uint32_t kColG = 0, kColB = 32, kColA = 48, kColC = 0, kColDl = 0, kColB0 = 16, kColR = 32, kColY = 64;
+//   pass B': c [0, 16), beta0 coefficients (24) [16, 40), r0 buffers 2 x (hi 8 | lo 8) [40, 72),
+//            fitted-value pieces 2 x 16 [72, 104)
+//   pass C : beta0 coefficients [16, 40), delta coefficients (24) [40, 64), pieces 2 x 32 [64, 128)
+constexpr uint32_t kColG = 0, kColB = 32, kColA = 48, kColC = 0, kColB0 = 16, kColR = 40, kColY0 = 72, kColDl = 40,
+                   kColY = 64;
+// Coefficient operands: 24 columns per set, A_hi (K = 32: 16 columns) then A_lo (K = 16: 8 columns).
+constexpr uint32_t kCoefLo = 16;
+// The regressors of the fitted-value table are scaled by 2^12 before their three-way fp16 split.
+constexpr float kYScale = 4096.f, kInvYScale = 1.f / 4096.f;
 
 template <typename T>
 struct Dt {
@@ -120,10 +125,11 @@ struct HybridParams {
 };
 
 // Byte offsets of the design tables in global memory for npad dates.
-__host__ __device__ inline size_t tab_gram_lo(int npad) { return (size_t)npad * 64; }
-__host__ __device__ inline size_t tab_x(int npad) { return (size_t)npad * 128; }
-__host__ __device__ inline size_t tab_yhat(int npad) { return (size_t)npad * 192; }
-__host__ __device__ inline size_t tab_bytes(int npad) { return (size_t)npad * 224; }
+__host__ __device__ inline size_t tab_gram_lo(int npad) { return (size_t)npad * 48; }
+__host__ __device__ inline size_t tab_x(int npad) { return (size_t)npad * 96; }
+__host__ __device__ inline size_t tab_yhat(int npad) { return (size_t)npad * 160; }
+__host__ __device__ inline size_t tab_yhat_bytes(int npad) { return (size_t)npad * 48 + 384; }
+__host__ __device__ inline size_t tab_bytes(int npad) { return tab_yhat(npad) + tab_yhat_bytes(npad); }
 
 struct HLayout {
     size_t gh, gl, xt, yh, stages, ring, bars, total;
@@ -138,10 +144,10 @@ __host__ __device__ inline HLayout hyb_layout(int n, int npad, int hmax) {
     const size_t nh16 = (size_t)((n + 15) & ~15);
     HLayout L{};
     L.gh = 0;
-    L.gl = L.gh + nh16 / 8 * 512;
-    L.xt = L.gl + nh16 / 8 * 512;
+    L.gl = L.gh + nh16 / 8 * 384;
+    L.xt = L.gl + nh16 / 8 * 384;
     L.yh = L.xt + nh16 / 4 * 256;
-    L.stages = up1024(L.yh + (size_t)npad / 8 * 256);
+    L.stages = up1024(L.yh + tab_yhat_bytes(npad));
     L.ring = L.stages + (size_t)kStages * kStageBytes;
     L.bars = L.ring + (size_t)hmax * kPx * 4;
     L.total = L.bars + (size_t)(2 * kStages + 13) * 8 + 16;
@@ -177,12 +183,14 @@ __device__ __forceinline__ void split_h(float x, __half& hi, float& lo) {
     lo = x - __half2float(hi);
 }
 
-// Coefficient A operands (fp16, K = 16) for the fitted-value table whose K
-// rows are [regressors hi; regressors lo]: A1 = [c_hi | c_hi], A2 = [c_lo | 0],
-// so that A1 B + A2 B = c_hi x_hi + c_hi x_lo + c_lo x_hi.  Returns the value
-// the products represent, c_hi + c_lo, in float.
+// Coefficient A operands (fp16) for the fitted-value table, whose K rows are
+// the regressors' three-way split [hi; mid; lo] (rows 24..31 are read from the
+// next date group and meet zeros here): A_hi = [c_hi | c_hi | c_hi | 0]
+// (K = 32, words 0..15) and A_lo = [c_lo | c_lo] (K = 16, words 16..23), so
+// that the products cover c_hi (hi + mid + lo) + c_lo (hi + mid).  Returns in
+// rep the value the products represent, c_hi + c_lo, in float.
 template <int K>
-__device__ __forceinline__ void coef_words(const float (&c)[K], float scale, uint32_t (&w)[16], float (&rep)[K]) {
+__device__ __forceinline__ void coef_words(const float (&c)[K], float scale, uint32_t (&w)[24], float (&rep)[K]) {
     __half hi[8], lo[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -200,9 +208,21 @@ __device__ __forceinline__ void coef_words(const float (&c)[K], float scale, uin
     for (int j = 0; j < 4; ++j) {
         w[j] = h2bits(hi[2 * j], hi[2 * j + 1]);
         w[4 + j] = w[j];
-        w[8 + j] = h2bits(lo[2 * j], lo[2 * j + 1]);
+        w[8 + j] = w[j];
         w[12 + j] = 0u;
+        w[16 + j] = h2bits(lo[2 * j], lo[2 * j + 1]);
+        w[20 + j] = w[16 + j];
     }
+}
+
+__device__ __forceinline__ void coef_store(uint32_t taddr, const uint32_t (&w)[24]) {
+    uint32_t a[16], b[8];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a[i] = w[i];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) b[i] = w[16 + i];
+    ptx::tmem_st16(taddr, a);
+    ptx::tmem_st8(taddr + kCoefLo, b);
 }
 
 // Bounded wait that also ends when the CTA aborts; false when it gave up.
@@ -425,10 +445,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint4* d = reinterpret_cast<uint4*>(dst);
             for (size_t i = tid; i < bytes / 16; i += kThreads) d[i] = __ldg(s + i);
         };
-        copy(s_gh, 0, nh16 / 8 * 512);
-        copy(s_gl, tab_gram_lo(npad), nh16 / 8 * 512);
+        copy(s_gh, 0, nh16 / 8 * 384);
+        copy(s_gl, tab_gram_lo(npad), nh16 / 8 * 384);
         copy(s_xt, tab_x(npad), nh16 / 4 * 256);
-        copy(s_yh, tab_yhat(npad), (size_t)npad / 8 * 256);
+        copy(s_yh, tab_yhat(npad), tab_yhat_bytes(npad));
     }
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -461,7 +481,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int64_t ntiles = (m + kPx - 1) / kPx;
     const int nst_h = (n + G - 1) / G;   // stages of one history pass
     const int nck = (n + 15) / 16;       // 16-date chunks of the history
-    const int npc_h = (n + 31) / 32;     // fitted-value pieces of the history
     auto dstart_of = [&](int v) -> int {
         const int d = v < n ? v : n;
         return d / G * G;
@@ -513,23 +532,31 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ---------------- tensor-core issuer
         if (lane == 0) {
             const uint32_t id_g = ptx::idesc_f16(128, 32, false), id_c = ptx::idesc_f16(128, 16, false);
-            const uint32_t id_x = ptx::idesc_tf32(128, 16), id_y = ptx::idesc_f16(128, 32, true);
+            const uint32_t id_x = ptx::idesc_tf32(128, 16);
+            const uint32_t id_y16 = ptx::idesc_f16(128, 16, true), id_y32 = ptx::idesc_f16(128, 32, true);
             uint32_t cc = 0, pc = 0, cpar = 0;
             bool ok = true;
-            // fitted values of dates [d0, d0 + 32) into piece buffer pc & 1
-            auto piece = [&](int d0, bool with_delta) -> bool {
+            // fitted values into piece buffer pc & 1: 16 dates of beta0 in pass B', 32 dates of
+            // beta0 + delta in pass C.  Per coefficient set: A_hi x rows 0..15, A_hi x rows 16..31,
+            // A_lo x rows 0..15 of the table (rows 16..31 start 256 bytes on).
+            auto piece = [&](int d0, bool pass_c) -> bool {
                 const uint32_t b = pc & 1u;
                 if (pc >= 2 && !wait_bar(yempty + b, ((pc >> 1) - 1) & 1u, abort_flag, kWaitNs)) return false;
                 ptx::tc_fence_after();
-                const uint64_t yd = ptx::smem_desc(s_yh + (size_t)(d0 / 8) * 256, 128, 256);
+                const uint64_t y01 = ptx::smem_desc(s_yh + (size_t)(d0 / 8) * 384, 128, 384);
+                const uint64_t y23 = ptx::smem_desc(s_yh + (size_t)(d0 / 8) * 384 + 256, 128, 384);
+                const uint32_t idy = pass_c ? id_y32 : id_y16;
 #pragma unroll
                 for (int g = 0; g < kMT; ++g) {
-                    const uint32_t base = tmem + 128u * g, dcol = base + kColY + 32u * b;
-                    ptx::mma_f16_ta(dcol, base + kColB0, yd, id_y, false);
-                    ptx::mma_f16_ta(dcol, base + kColB0 + 8, yd, id_y, true);
-                    if (with_delta) {
-                        ptx::mma_f16_ta(dcol, base + kColDl, yd, id_y, true);
-                        ptx::mma_f16_ta(dcol, base + kColDl + 8, yd, id_y, true);
+                    const uint32_t base = tmem + 128u * g;
+                    const uint32_t dcol = pass_c ? base + kColY + 32u * b : base + kColY0 + 16u * b;
+                    ptx::mma_f16_ta(dcol, base + kColB0, y01, idy, false);
+                    ptx::mma_f16_ta(dcol, base + kColB0 + 8, y23, idy, true);
+                    ptx::mma_f16_ta(dcol, base + kColB0 + kCoefLo, y01, idy, true);
+                    if (pass_c) {
+                        ptx::mma_f16_ta(dcol, base + kColDl, y01, idy, true);
+                        ptx::mma_f16_ta(dcol, base + kColDl + 8, y23, idy, true);
+                        ptx::mma_f16_ta(dcol, base + kColDl + kCoefLo, y01, idy, true);
                     }
                 }
                 ptx::mma_commit(yfull + b);
@@ -548,8 +575,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int c = 0; c < nck && ok; ++c) {
                     if (!(ok = wait_a())) break;
                     const uint32_t b = cc & 1u;
-                    const uint64_t gh = ptx::smem_desc(s_gh + (size_t)(2 * c) * 512, 512, 128);
-                    const uint64_t gl = ptx::smem_desc(s_gl + (size_t)(2 * c) * 512, 512, 128);
+                    const uint64_t gh = ptx::smem_desc(s_gh + (size_t)(2 * c) * 384, 384, 128);
+                    const uint64_t gl = ptx::smem_desc(s_gl + (size_t)(2 * c) * 384, 384, 128);
                     const uint64_t x0 = ptx::smem_desc(s_xt + (size_t)(4 * c) * 256, 256, 128);
                     const uint64_t x1 = ptx::smem_desc(s_xt + (size_t)(4 * c + 2) * 256, 256, 128);
 #pragma unroll
@@ -569,13 +596,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!(ok = wait_bar(coefb, cpar, abort_flag, kWaitNs))) break;
                 cpar ^= 1u;
                 ptx::tc_fence_after();
-                int ip = 0;
-                for (; ip < 2 && ip < npc_h && ok; ++ip) ok = piece(32 * ip, false);
+                for (int c = 0; c < 2 && c < nck && ok; ++c) ok = piece(16 * c, false);
                 for (int c = 0; c < nck && ok; ++c) {
                     if (!(ok = wait_a())) break;
                     const uint32_t b = cc & 1u;
-                    const uint64_t gh = ptx::smem_desc(s_gh + (size_t)(2 * c) * 512, 512, 128);
-                    const uint64_t gl = ptx::smem_desc(s_gl + (size_t)(2 * c) * 512, 512, 128);
+                    const uint64_t gh = ptx::smem_desc(s_gh + (size_t)(2 * c) * 384, 384, 128);
+                    const uint64_t gl = ptx::smem_desc(s_gl + (size_t)(2 * c) * 384, 384, 128);
 #pragma unroll
                     for (int g = 0; g < kMT; ++g) {
                         const uint32_t base = tmem + 128u * g, a = base + kColR + 16u * b;
@@ -585,11 +611,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     ptx::mma_commit(aempty + b);
                     ++cc;
-                    // after the last chunk of a piece the pixel warps are done with that piece
-                    if (((c & 1) == 1 || c == nck - 1) && ip < npc_h) {
-                        ok = piece(32 * ip, false);
-                        ++ip;
-                    }
+                    // the pixel warps read chunk c's fitted values before they wrote its A operands
+                    if (c + 2 < nck) ok = piece(16 * (c + 2), false);
                 }
                 if (!ok) break;
                 ptx::mma_commit(cdone);
@@ -760,13 +783,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             const float inv_sb = 1.f / s_b, inv_sr = 1.f / s_r;
+            const float inv_fit = inv_sb * kInvYScale;  // the fitted values come out scaled by s_b 2^12
             {
-                uint32_t wv[16];
+                uint32_t wv[24];
                 float rep[K];
                 coef_words<K>(b0, s_b, wv, rep);
 #pragma unroll
                 for (int a = 0; a < K; ++a) b0[a] = rep[a] * inv_sb;  // beta0 as the MMAs see it
-                ptx::tmem_st16(tl + tcol + kColB0, wv);
+                coef_store(tl + tcol + kColB0, wv);
                 ptx::tmem_wait_st();
                 arrive(coefb);
             }
@@ -781,14 +805,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             float ss0 = 0.f;
             int rem = wq, wdate = n;
             for (int c = 0; c < nck && !bad; ++c) {
-                if ((c & 1) == 0 && !wait_w(yfull + (pc & 1u), (pc >> 1) & 1u)) break;
+                if (!wait_w(yfull + (pc & 1u), (pc >> 1) & 1u)) break;
                 ptx::tc_fence_after();
                 float yh[16];
-                ptx::tmem_ld16(tl + tcol + kColY + 32u * (pc & 1u) + 16u * (uint32_t)(c & 1), yh);
-                if ((c & 1) == 1 || c == nck - 1) {
-                    arrive(yempty + (pc & 1u));
-                    ++pc;
-                }
+                ptx::tmem_ld16(tl + tcol + kColY0 + 16u * (pc & 1u), yh);
+                arrive(yempty + (pc & 1u));
+                ++pc;
                 const uint32_t b = cc & 1u;
                 if (cc >= 2 && !wait_w(aempty + b, ((cc >> 1) - 1) & 1u)) break;
                 ptx::tc_fence_after();
@@ -805,17 +827,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const bool fullb = d8 + 8 <= n;
                         if (scan) {
                             if (fullb)
-                                pass_b8<true, true>(ob, st, d8, n, yh + 8 * h, inv_sb, s_r, ss0, hw + 4 * h,
+                                pass_b8<true, true>(ob, st, d8, n, yh + 8 * h, inv_fit, s_r, ss0, hw + 4 * h,
                                                     lw + 4 * h, rem, wdate);
                             else
-                                pass_b8<false, true>(ob, st, d8, n, yh + 8 * h, inv_sb, s_r, ss0, hw + 4 * h,
+                                pass_b8<false, true>(ob, st, d8, n, yh + 8 * h, inv_fit, s_r, ss0, hw + 4 * h,
                                                      lw + 4 * h, rem, wdate);
                         } else {
                             if (fullb)
-                                pass_b8<true, false>(ob, st, d8, n, yh + 8 * h, inv_sb, s_r, ss0, hw + 4 * h,
+                                pass_b8<true, false>(ob, st, d8, n, yh + 8 * h, inv_fit, s_r, ss0, hw + 4 * h,
                                                      lw + 4 * h, rem, wdate);
                             else
-                                pass_b8<false, false>(ob, st, d8, n, yh + 8 * h, inv_sb, s_r, ss0, hw + 4 * h,
+                                pass_b8<false, false>(ob, st, d8, n, yh + 8 * h, inv_fit, s_r, ss0, hw + 4 * h,
                                                       lw + 4 * h, rem, wdate);
                         }
                         if (G == 8 || h == 1 || d8 + 8 >= n) release();
@@ -880,10 +902,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 float dfin[K];
 #pragma unroll
                 for (int a = 0; a < K; ++a) dfin[a] = (fit && isfinite(dl[a])) ? dl[a] : 0.f;
-                uint32_t wv[16];
+                uint32_t wv[24];
                 float rep[K];
                 coef_words<K>(dfin, s_b, wv, rep);
-                ptx::tmem_st16(tl + tcol + kColDl, wv);
+                coef_store(tl + tcol + kColDl, wv);
             }
             // the tile's earliest window start, for the producer and the MMA warp
             {
@@ -912,7 +934,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mo.hp_off = hp * kPx;
             mo.fill_end = (hp - 1) * kPx;
             mo.wdate = wdate;
-            mo.inv_sb = inv_sb;
+            mo.inv_sb = inv_fit;
             ring_t[(hp - 1) * kPx] = 0.f;  // the first monitoring step finds h_p - 1 residuals
             int brk = -1;
             float sh = 0.f, sl = 0.f;
@@ -1044,11 +1066,17 @@ int hyb_npad(int N) { return (N + 31) / 32 * 32 + 32; }
 
 // Design tables of the hybrid form for npad = hyb_npad(N) dates (zero beyond N):
 //   Gram hi, Gram lo: the 3 + 6k basis functions (bfm::Basis order) split fp16
-//     hi + lo, K-major over dates: (t/8)*512 + (r/8)*128 + (r%8)*16 + (t%8)*2;
+//     hi + lo, K-major over dates, three 8-row groups per 8-date group:
+//     (t/8)*384 + (r/8)*128 + (r%8)*16 + (t%8)*2 (an MMA with N = 32 reads its
+//     fourth row group from the next date group: accumulator columns 24..31,
+//     which nothing reads);
 //   X: the K regressors as tf32 hi (rows 0..7) and lo = x - hi (rows 8..15),
 //     K-major over dates: (t/4)*256 + (r/8)*128 + (r%8)*16 + (t%4)*4;
-//   fitted values: the K regressors fp16 hi (rows 0..7) and lo (rows 8..15),
-//     read MN-major: (t/8)*256 + (r/8)*128 + (r%8)*16 + (t%8)*2.
+//   fitted values: the K regressors times 2^12 split three ways into fp16 hi
+//     (rows 0..7), mid (8..15) and lo (16..23), read MN-major:
+//     (t/8)*384 + (r/8)*128 + (r%8)*16 + (t%8)*2, plus one group of zeros at
+//     the end (rows 24..31 of the last group are read from it and meet zero
+//     coefficients).
 void hybrid_tables(const bfm_design_s& d, const std::vector<double>& rows, std::vector<unsigned char>& out) {
     const int npad = hyb_npad(d.N), nbr = 3 + 6 * d.k, K = d.K;
     out.assign(tab_bytes(npad), 0);
@@ -1061,7 +1089,7 @@ void hybrid_tables(const bfm_design_s& d, const std::vector<double>& rows, std::
             const double v = rows[(size_t)t * d.NB + r];
             const __half hi = __double2half(v);
             const __half lo = __double2half(v - (double)__half2float(hi));
-            const size_t o = (size_t)(t / 8) * 512 + (size_t)(r / 8) * 128 + (size_t)(r % 8) * 16 + (size_t)(t % 8) * 2;
+            const size_t o = (size_t)(t / 8) * 384 + (size_t)(r / 8) * 128 + (size_t)(r % 8) * 16 + (size_t)(t % 8) * 2;
             std::memcpy(gh + o, &hi, 2);
             std::memcpy(gl + o, &lo, 2);
         }
@@ -1077,10 +1105,15 @@ void hybrid_tables(const bfm_design_s& d, const std::vector<double>& rows, std::
             const float lof = (float)(v - (double)hif);
             std::memcpy(xt + (size_t)(t / 4) * 256 + (size_t)(r % 8) * 16 + (size_t)(t % 4) * 4, &hif, 4);
             std::memcpy(xt + (size_t)(t / 4) * 256 + 128 + (size_t)(r % 8) * 16 + (size_t)(t % 4) * 4, &lof, 4);
-            const __half hh = __double2half(v);
-            const __half hl = __double2half(v - (double)__half2float(hh));
-            std::memcpy(yh + (size_t)(t / 8) * 256 + (size_t)(r % 8) * 16 + (size_t)(t % 8) * 2, &hh, 2);
-            std::memcpy(yh + (size_t)(t / 8) * 256 + 128 + (size_t)(r % 8) * 16 + (size_t)(t % 8) * 2, &hl, 2);
+            const double vs = v * (double)kYScale;
+            const __half h1 = __double2half(vs);
+            const double r1 = vs - (double)__half2float(h1);
+            const __half h2 = __double2half(r1);
+            const __half h3 = __double2half(r1 - (double)__half2float(h2));
+            const size_t oy = (size_t)(t / 8) * 384 + (size_t)(r % 8) * 16 + (size_t)(t % 8) * 2;
+            std::memcpy(yh + oy, &h1, 2);
+            std::memcpy(yh + oy + 128, &h2, 2);
+            std::memcpy(yh + oy + 256, &h3, 2);
         }
     }
 }

@@ -214,7 +214,10 @@ void start(bfm_server_s* s, Req* q, int slot) {
             const bool ok = mma_supported(r.design, r.dtype, r.n_hist, r.h_frac, Y, r.m, nullptr);
             algo = ok ? BFM_ALGO_MMA : BFM_ALGO_SIMT;
         }
-        bs = algo == BFM_ALGO_STREAM
+        bs = algo == BFM_ALGO_HYBRID
+                 ? launch_hybrid(r.design, r.dtype, Y, r.mask_bits, r.m, r.n_hist, r.h_frac, r.lambda, q->brk, q->mean,
+                                 q->sigma, q->beta, q->status, st, nullptr)
+             : algo == BFM_ALGO_STREAM
                  ? launch_stream(r.design, r.dtype, Y, r.mask_bits, r.m, r.n_hist, r.h_frac, r.lambda, q->brk, q->mean,
                                  q->sigma, q->beta, q->status, st, nullptr)
              : algo == BFM_ALGO_COMPLETE
@@ -318,7 +321,7 @@ bfm_status bfm_serve_submit(bfm_server_t s, const bfm_serve_request* r, uint64_t
     const bfm_design_s* d = r->design;
     if ((r->dtype != BFM_F32 && r->dtype != BFM_I16) || r->m < 0 || !(r->n_hist >= 1 && r->n_hist < d->N) ||
         !(r->h_frac > 0.0 && r->h_frac <= 1.0) || !(r->lambda > 0.0) || (r->m > 0 && !r->Y) ||
-        !(r->algo >= BFM_ALGO_AUTO && r->algo <= BFM_ALGO_STREAM)) {
+        !(r->algo >= BFM_ALGO_AUTO && r->algo <= BFM_ALGO_HYBRID)) {
         set_error("bfm_serve_submit: bad dtype, m, n_hist, h_frac, lambda, algo or NULL Y");
         return BFM_EINVAL;
     }

@@ -1,6 +1,6 @@
 """CUDA path vs FP64 oracle, element by element, through the C ABI, in the
-three general forms (CUDA-core, tensor-core, streaming CUDA-core) on float
-storage.
+four general forms (CUDA-core, tensor-core, streaming CUDA-core, hybrid) on
+float storage.
 
 Float path tolerance 1e-5 (beta column-scaled, sigma relative, mean MOSUM
 relative to max(1, |ref|)); break indices equal except on margin-tied pixels.
@@ -48,7 +48,7 @@ def _check(w, Y, gpu, *, k=None, mask=None, tol=TOL_F32):
     return rep, ref
 
 
-ALGOS = pytest.mark.parametrize("algo", [1, 2, 4], ids=["simt", "mma", "stream"])
+ALGOS = pytest.mark.parametrize("algo", [1, 2, 4, 5], ids=["simt", "mma", "stream", "hybrid"])
 
 
 @ALGOS
@@ -93,7 +93,7 @@ def test_c1_mask_bits(bfm, algo):
     _check(w, w["Y"], gpu, mask=bits)
 
 
-@pytest.mark.parametrize("algo", [1, 4], ids=["simt", "stream"])
+@pytest.mark.parametrize("algo", [1, 4, 5], ids=["simt", "stream", "hybrid"])
 def test_c3_int16_simt(bfm, algo):
     """int16 storage (NDVI*1e4, -32768 missing) on the CUDA-core paths."""
     w = synth.workload("c3")
@@ -217,7 +217,7 @@ def c2_full(bfm):
     Yd = torch.from_numpy(w["Y"]).cuda()
     d = bfm.Design(w["dates"], 3, 23.0)
     res = {}
-    for algo in (1, 2, 4):
+    for algo in (1, 2, 4, 5):
         out = bfm.monitor(d, Yd, n_hist=w["n_hist"], h_frac=w["h_frac"], lam=w["lam"], algo=algo)
         torch.cuda.synchronize()
         assert bfm.bfm_device_errors() == 0
