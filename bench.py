@@ -265,8 +265,7 @@ def run_tiles_and_serving(bfm, synth, torch, dev, stream):
                                     device=dev)
         design = bfm.Design(d, t["k"], 23.0)
         tiles.append(dict(t, Y=Y, design=design, lam=synth.lambda_for_horizon(t["N"] / t["n_hist"]),
-                          out=bfm.empty_outputs(2 + 2 * t["k"], t["m"], dev),
-                          mma=bfm.bfm_batch_form(design, bfm.BFM_I16, t["n_hist"], 0.25, Y, t["m"]) == bfm.BFM_ALGO_MMA))
+                          out=bfm.empty_outputs(2 + 2 * t["k"], t["m"], dev)))
     total_px = sum(t["m"] for t in tiles)
     torch.cuda.synchronize()
 
@@ -292,29 +291,42 @@ def run_tiles_and_serving(bfm, synth, torch, dev, stream):
     lat.sort()
     c4 = {"workload": "c4: 64 int16 tiles, pixels log-U[1e4, 2e6] rounded up to multiples of 8, N ~ U{120..600}, "
                       "k ~ U{1..3}, history U(0.4, 0.7), Markov clouds 20-70 %",
-          "pixels": total_px, "tiles_tensor_core_form": sum(t["mma"] for t in tiles),
+          "pixels": total_px,
           "per_tile_calls": {"value": 3 * total_px / (tot / 1e3), "unit": "pixels/s",
                              "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1,
                                             int(math.ceil(0.99 * len(lat))) - 1)], "unit": "one tile"}}}
-    b = bfm.Batch()
-    bouts = []
-    for t in tiles:
-        bouts.append(b.add(t["design"], t["Y"], n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"]))
-    b.autotune(stream)
-    b.run(stream)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(5):
+    names = {bfm.BFM_ALGO_HYBRID: "hybrid", bfm.BFM_ALGO_MMA: "tensor_core", bfm.BFM_ALGO_SIMT: "cuda_core"}
+
+    def batched(forms):
+        b = bfm.Batch(forms=forms)
+        bouts = []
+        for t in tiles:
+            bouts.append(b.add(t["design"], t["Y"], n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"]))
+        by_form = {}
+        for i, t in enumerate(tiles):
+            f = names[b.form(i)]
+            by_form[f] = by_form.get(f, 0) + t["m"]
+        b.autotune(stream)
         b.run(stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    bms = e0.elapsed_time(e1) / 5
-    c4["batched_launch"] = {"value": total_px / (bms / 1e3), "unit": "pixels/s", "ms_per_batch": bms,
-                            "form": "one CUDA-graph replay: persistent tensor-core kernels per (k, storage, "
-                                    "CTAs per SM) group and the persistent CUDA-core kernel"}
-    b.close()
-    del bouts
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(5):
+            b.run(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bms = e0.elapsed_time(e1) / 5
+        b.close()
+        del bouts
+        return {"value": total_px / (bms / 1e3), "unit": "pixels/s", "ms_per_batch": bms, "pixels_by_form": by_form}
+
+    c4["batched_launch"] = dict(batched(bfm.BFM_ALGO_AUTO),
+                                form="one CUDA-graph replay: persistent hybrid kernels per (k, storage, layout) "
+                                     "group, persistent tensor-core kernels per (k, storage, CTAs per SM) group for "
+                                     "the tiles whose ring does not fit the hybrid form, the CUDA-core kernel for "
+                                     "the rest")
+    c4["batched_launch_tensor_core_forms"] = dict(batched(bfm.BFM_ALGO_MMA),
+                                                  form="the same batch limited to the tensor-core and CUDA-core forms")
 
     c5 = {"workload": "c5: the c4 tiles from device memory, Poisson arrivals", "rates": {}}
     rng = np.random.default_rng(5)

@@ -296,10 +296,12 @@ bfm_status bfm_monitor_host(bfm_design_t d, const void *Y_host, int dtype, const
 /*
  * Batched persistent launch -- many scene tiles of uneven pixel counts,
  * series lengths (their own designs), harmonics and storage types processed
- * by one CUDA-graph replay of persistent kernels: one per tensor-core kernel
- * variant (k, storage, mask) for the tiles the tensor-core form takes
- * (128-pixel blocks), and one CUDA-core kernel for the rest (32-pixel
- * blocks); bfm_batch_form tells which.  The paper processes one scene per
+ * by one CUDA-graph replay of persistent kernels: one per hybrid kernel
+ * variant (k, storage, mask) and shared-memory layout for the tiles the
+ * hybrid form takes (512-pixel blocks, taken in a fixed order), one per
+ * tensor-core kernel variant for the tiles the tensor-core form takes
+ * (128-pixel blocks from a work counter), and one CUDA-core kernel for the
+ * rest (32-pixel blocks); bfm_batch_form and bfm_batch_tile_form tell which.  The paper processes one scene per
  * call (Algorithm 2); batching is a serving extension with the same
  * per-pixel results: every pixel's outputs equal those of bfm_monitor_ex
  * with the form bfm_batch_form names, on its tile alone.
@@ -311,10 +313,12 @@ bfm_status bfm_monitor_host(bfm_design_t d, const void *Y_host, int dtype, const
  *                       receives its index.  The batch holds a reference to
  *                       the design.
  *   bfm_batch_run       enqueues the whole batch on `stream`: a graph of the
- *                       work-counter resets, the tensor-core kernels (a chain;
- *                       up to 2 CTAs per SM each) and the CUDA-core kernel (a
- *                       parallel branch; CTAs = SM count x CTAs per SM, taking
- *                       `grab` 32-pixel blocks at a time).  The first run after adds uploads the tile
+ *                       work-counter resets, the hybrid kernels (one CTA per
+ *                       SM) and the tensor-core kernels (up to 2 CTAs per SM),
+ *                       a chain, and the CUDA-core kernel (CTAs = SM count x
+ *                       CTAs per SM, taking `grab` 32-pixel blocks at a time;
+ *                       after the chain when the batch has hybrid tiles, else
+ *                       a parallel branch).  The first run after adds uploads the tile
  *                       table and instantiates the graph; later runs replay it.
  *   bfm_batch_autotune  times every (CTAs per SM, grab in {1,2,4,8})
  *                       candidate on this batch (3 replays each, CUDA events on
@@ -334,9 +338,19 @@ bfm_status bfm_batch_run(bfm_batch_t b, void *stream);
 bfm_status bfm_batch_autotune(bfm_batch_t b, void *stream, int *ctas_per_sm, int *grab, float *best_ms);
 bfm_status bfm_batch_set_config(bfm_batch_t b, int ctas_per_sm, int grab);
 int bfm_batch_tiles(bfm_batch_t b);
-/* The form a tile with these arguments takes in a batch: BFM_ALGO_MMA or
- * BFM_ALGO_SIMT (no work, no device access). */
+/* The form a tile with these arguments takes in a batch whose forms are
+ * BFM_ALGO_AUTO: BFM_ALGO_HYBRID, BFM_ALGO_MMA or BFM_ALGO_SIMT (no work, no
+ * device access). */
 int bfm_batch_form(bfm_design_t d, int dtype, int n_hist, double h_frac, const void *Y, int64_t m);
+/* The forms tiles added later may take: BFM_ALGO_AUTO (the default: the
+ * hybrid form where it applies, else the tensor-core form, else the
+ * CUDA-core form), BFM_ALGO_HYBRID (hybrid, else CUDA-core), BFM_ALGO_MMA
+ * (tensor-core, else CUDA-core) or BFM_ALGO_SIMT (CUDA-core only).
+ * BFM_EINVAL for any other value or once the batch holds tiles. */
+bfm_status bfm_batch_set_forms(bfm_batch_t b, int algo);
+/* The form tile `tile_id` (bfm_batch_add's *tile_id) takes in this batch, a
+ * BFM_ALGO_* value; -1 for a NULL batch or an unknown id. */
+int bfm_batch_tile_form(bfm_batch_t b, int tile_id);
 bfm_status bfm_batch_destroy(bfm_batch_t b);
 
 /*

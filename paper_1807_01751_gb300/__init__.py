@@ -127,6 +127,10 @@ def load(build_if_missing: bool = True):
         lib.bfm_batch_set_config.restype = i32
         lib.bfm_batch_tiles.argtypes = [vp]
         lib.bfm_batch_tiles.restype = i32
+        lib.bfm_batch_set_forms.argtypes = [vp, i32]
+        lib.bfm_batch_set_forms.restype = i32
+        lib.bfm_batch_tile_form.argtypes = [vp, i32]
+        lib.bfm_batch_tile_form.restype = i32
         lib.bfm_batch_destroy.argtypes = [vp]
         lib.bfm_batch_destroy.restype = i32
         lib.bfm_batch_run_static.argtypes = [ctypes.POINTER(TileSpec), i32, vp]
@@ -310,6 +314,14 @@ def bfm_batch_set_config(batch, ctas_per_sm: int, grab: int):
     _check(load().bfm_batch_set_config(int(batch), int(ctas_per_sm), int(grab)))
 
 
+def bfm_batch_set_forms(batch, algo: int):
+    _check(load().bfm_batch_set_forms(int(batch), int(algo)))
+
+
+def bfm_batch_tile_form(batch, tile_id: int) -> int:
+    return load().bfm_batch_tile_form(int(batch), int(tile_id))
+
+
 def bfm_batch_destroy(batch):
     _check(load().bfm_batch_destroy(int(batch)))
 
@@ -414,9 +426,12 @@ class Batch:
     """Owning wrapper of a bfm_batch_t: tiles added with :meth:`add` run in one
     persistent launch (:meth:`run`), replayed from a CUDA graph."""
 
-    def __init__(self):
+    def __init__(self, forms: int = BFM_ALGO_AUTO):
         self.handle = bfm_batch_create()
         self.tiles = []
+        self.ids = []
+        if forms != BFM_ALGO_AUTO:
+            bfm_batch_set_forms(self.handle, forms)
 
     def add(self, design: Design, Y, *, n_hist: int, h_frac: float, lam: float, mask_bits=None, out=None):
         import torch
@@ -424,10 +439,15 @@ class Batch:
         m = Y.shape[1]
         if out is None:
             out = empty_outputs(design.K, m, Y.device)
-        bfm_batch_add(self.handle, design, Y, dtype, mask_bits, m, n_hist, h_frac, lam, out["break_idx"],
-                      out["mean_mosum"], out["sigma"], out["beta"], out["status"])
+        tid = bfm_batch_add(self.handle, design, Y, dtype, mask_bits, m, n_hist, h_frac, lam, out["break_idx"],
+                            out["mean_mosum"], out["sigma"], out["beta"], out["status"])
         self.tiles.append((Y, mask_bits, out))  # keep buffers alive
+        self.ids.append(tid)
         return out
+
+    def form(self, i: int) -> int:
+        """The form the i-th added tile takes in this batch (BFM_ALGO_*)."""
+        return bfm_batch_tile_form(self.handle, self.ids[i])
 
     def run(self, stream=None):
         bfm_batch_run(self.handle, stream)

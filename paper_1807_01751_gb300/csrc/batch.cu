@@ -1,13 +1,18 @@
 // Batched persistent launch: many scene tiles of uneven pixel counts, series
 // lengths, harmonics and storage types in one CUDA-graph replay.
 //
-// Each tile takes the form bfm_monitor's AUTO would take.  Tensor-core tiles
-// are grouped by kernel variant (k, storage, mask); per variant a persistent
-// grid (up to 2 CTAs per SM) takes 128-pixel blocks from a device counter and
-// finds the owning tile by binary search.  The CUDA-core tiles go to one
-// persistent kernel whose CTAs take 32-pixel blocks, `grab` at a time, in the
-// same way.  The counter resets (one memset node), the tensor-core variants
-// (a chain) and the CUDA-core kernel (a parallel branch) form one graph,
+// Each tile takes the first form of hybrid, tensor-core, CUDA-core that
+// applies (bfm_batch_set_forms narrows the choice).  Hybrid tiles are grouped
+// by kernel variant (k, storage, mask) and a shared-memory layout that holds
+// the group's largest tables and ring; per group one persistent kernel (one
+// CTA per SM) takes 512-pixel blocks in a fixed order and finds the owning
+// tile by binary search (hybrid.cu).  Tensor-core tiles are grouped by kernel
+// variant; per variant a persistent grid (up to 2 CTAs per SM) takes 128-pixel
+// blocks from a device counter and finds the owning tile the same way.  The
+// CUDA-core tiles go to one persistent kernel whose CTAs take 32-pixel blocks,
+// `grab` at a time.  The counter resets (one memset node), the hybrid and
+// tensor-core kernels (a chain) and the CUDA-core kernel (after the chain
+// when there are hybrid tiles, else a parallel branch) form one graph,
 // instantiated once and replayed.  An autotuner times (CTAs per SM, grab) for
 // the CUDA-core kernel on the batch itself and caches the best pair per batch
 // signature.
@@ -46,7 +51,11 @@ struct bfm_batch_s {
     std::vector<bfm::MmaBatchTile> mtiles[kGroups];
     int64_t mblocks[kGroups] = {};
     size_t msmem[kGroups] = {};
+    // hybrid tiles, per group = kernel variant x shared-memory layout
+    std::vector<bfm::HybGroup*> hgroups;
     int ntiles_all = 0;
+    int forms = BFM_ALGO_AUTO;  // the forms tiles may take (bfm_batch_set_forms)
+    std::vector<int> tile_form;  // per tile id: the form it takes
     std::vector<bfm_design_t> designs;  // references held until destroy
     // device copies
     void* d_tiles = nullptr;
@@ -104,6 +113,10 @@ bfm_status upload(bfm_batch_s* b) {
     size_t nm = 0;
     for (int v = 0; v < bfm_batch_s::kGroups; ++v) nm += b->mtiles[v].size();
     cudaError_t e = cudaSuccess;
+    for (auto* g : b->hgroups) {
+        const bfm_status st = hyb_group_upload(g);
+        if (st != BFM_OK) return st;
+    }
     if (!b->tiles.empty()) e = cudaMalloc(&b->d_tiles, sizeof(BatchTileDesc) * b->tiles.size());
     if (e == cudaSuccess && !b->tmaps.empty()) e = cudaMalloc(&b->d_tmaps, sizeof(CUtensorMap) * b->tmaps.size());
     if (e == cudaSuccess && nm) e = cudaMalloc(&b->d_mtiles, sizeof(MmaBatchTile) * nm);
@@ -156,8 +169,14 @@ bfm_status build_graph(bfm_batch_s* b, int grid, int grab) {
     e = cudaGraphAddMemsetNode(&memset_node, b->graph, nullptr, 0, &mp);
     if (e != cudaSuccess) return cuda_fail(e, "bfm_batch: memset node");
     bfm_status st = BFM_OK;
-    // tensor-core groups: a chain after the memset
+    // hybrid groups, then the tensor-core groups: a chain after the memset
     cudaGraphNode_t prev = memset_node;
+    for (auto* g : b->hgroups) {
+        cudaGraphNode_t node;
+        st = hyb_group_node(g, b->graph, &prev, &node);
+        if (st != BFM_OK) return st;
+        prev = node;
+    }
     size_t off = 0;
     for (int v = 0; v < bfm_batch_s::kGroups; ++v) {
         if (b->mtiles[v].empty()) continue;
@@ -169,10 +188,12 @@ bfm_status build_graph(bfm_batch_s* b, int grid, int grab) {
         prev = node;
         off += b->mtiles[v].size();
     }
-    // CUDA-core tiles: a parallel branch
+    // CUDA-core tiles: a parallel branch beside the tensor-core kernels, or after the hybrid
+    // kernels, whose CTAs take their work blocks in a fixed order and so should find every SM free
     if (!b->tiles.empty() && b->total_blocks > 0) {
+        const cudaGraphNode_t dep = b->hgroups.empty() ? memset_node : prev;
         st = batch_launch_kernel(b->d_tiles, b->d_tmaps, (int)b->tiles.size(), b->total_blocks, b->d_counter, grab,
-                                 grid, b->smem, nullptr, b->graph, &memset_node, &kernel_node);
+                                 grid, b->smem, nullptr, b->graph, &dep, &kernel_node);
         if (st != BFM_OK) return st;
     }
     e = cudaGraphInstantiate(&b->exec, b->graph, 0);
@@ -217,6 +238,7 @@ bfm_status bfm_batch_destroy(bfm_batch_t b) {
         return BFM_EINVAL;
     }
     free_dev(b);
+    for (auto* g : b->hgroups) hyb_group_destroy(g);
     for (auto d : b->designs) bfm_design_destroy(d);
     delete b;
     return BFM_OK;
@@ -241,7 +263,41 @@ bfm_status bfm_batch_add(bfm_batch_t b, bfm_design_t d, const void* Y, int dtype
         set_error("bfm_batch_add: Y and all outputs must be non-NULL device pointers");
         return BFM_EINVAL;
     }
-    if (m > 0 && mma_supported(d, dtype, n_hist, h_frac, Y, m, nullptr)) {
+    // keep the design alive while the batch may run
+    auto hold = [&](int form) {
+        bfm_design_t dd = nullptr;
+        bfm_design_create(d->dates.data(), d->N, d->k, d->f, &dd);
+        b->designs.push_back(dd);
+        b->dirty = true;
+        b->tile_form.push_back(form);
+        if (tile_id) *tile_id = b->ntiles_all;
+        ++b->ntiles_all;
+        return BFM_OK;
+    };
+    const bool hyb_ok = b->forms == BFM_ALGO_AUTO || b->forms == BFM_ALGO_HYBRID;
+    const bool mma_ok = b->forms == BFM_ALGO_AUTO || b->forms == BFM_ALGO_MMA;
+    if (hyb_ok && m > 0 && hybrid_supported(d, dtype, n_hist, h_frac, Y, m)) {
+        // the hybrid form: the first group of this variant whose layout still fits, else a new one
+        const bool hm = mask_bits != nullptr;
+        for (auto* g : b->hgroups) {
+            if (!hyb_group_variant(g, d->k, dtype, hm)) continue;
+            const int r = hyb_group_add(g, d, Y, mask_bits, m, n_hist, h_frac, lambda, break_idx, mean_mosum, sigma,
+                                        beta, status);
+            if (r < 0) return BFM_EUNSUPPORTED;
+            if (r > 0) return hold(BFM_ALGO_HYBRID);
+        }
+        HybGroup* g = hyb_group_create(d->k, dtype, hm);
+        const int r = hyb_group_add(g, d, Y, mask_bits, m, n_hist, h_frac, lambda, break_idx, mean_mosum, sigma, beta,
+                                    status);
+        if (r <= 0) {
+            hyb_group_destroy(g);
+            if (r == 0) set_error("bfm_batch_add: the tile does not fit the hybrid form's shared memory");
+            return BFM_EUNSUPPORTED;
+        }
+        b->hgroups.push_back(g);
+        return hold(BFM_ALGO_HYBRID);
+    }
+    if (mma_ok && m > 0 && mma_supported(d, dtype, n_hist, h_frac, Y, m, nullptr)) {
         // the tensor-core form, as bfm_monitor's AUTO would take it
         MmaBatchTile mt;
         size_t msm = 0;
@@ -254,13 +310,7 @@ bfm_status bfm_batch_add(bfm_batch_t b, bfm_design_t d, const void* Y, int dtype
         b->mtiles[v].push_back(mt);
         b->mblocks[v] += (m + 127) / 128;
         b->msmem[v] = std::max(b->msmem[v], msm);
-        bfm_design_t dd = nullptr;
-        bfm_design_create(d->dates.data(), d->N, d->k, d->f, &dd);
-        b->designs.push_back(dd);
-        b->dirty = true;
-        if (tile_id) *tile_id = b->ntiles_all;
-        ++b->ntiles_all;
-        return BFM_OK;
+        return hold(BFM_ALGO_MMA);
     }
     int br = 0, nb = 0;
     const size_t smem = simt_smem_bytes(d->N, d->k, dtype, &br, &nb);
@@ -299,14 +349,7 @@ bfm_status bfm_batch_add(bfm_batch_t b, bfm_design_t d, const void* Y, int dtype
     b->tmaps.push_back(tm);
     b->total_blocks += (m + 31) / 32;
     b->smem = std::max(b->smem, smem);
-    // keep the design alive while the batch may run
-    bfm_design_t dd = nullptr;
-    bfm_design_create(d->dates.data(), d->N, d->k, d->f, &dd);
-    b->designs.push_back(dd);
-    b->dirty = true;
-    if (tile_id) *tile_id = b->ntiles_all;
-    ++b->ntiles_all;
-    return BFM_OK;
+    return hold(BFM_ALGO_SIMT);
 }
 
 bfm_status bfm_batch_run(bfm_batch_t b, void* stream) {
@@ -399,7 +442,30 @@ int bfm_batch_tiles(bfm_batch_t b) { return b ? b->ntiles_all : 0; }
 
 int bfm_batch_form(bfm_design_t d, int dtype, int n_hist, double h_frac, const void* Y, int64_t m) {
     if (!d || (dtype != BFM_F32 && dtype != BFM_I16) || !(n_hist >= 1 && n_hist < d->N)) return BFM_ALGO_SIMT;
-    return mma_supported(d, dtype, n_hist, h_frac, Y, m, nullptr) ? BFM_ALGO_MMA : BFM_ALGO_SIMT;
+    if (m > 0 && hybrid_supported(d, dtype, n_hist, h_frac, Y, m)) return BFM_ALGO_HYBRID;
+    return m > 0 && mma_supported(d, dtype, n_hist, h_frac, Y, m, nullptr) ? BFM_ALGO_MMA : BFM_ALGO_SIMT;
+}
+
+bfm_status bfm_batch_set_forms(bfm_batch_t b, int algo) {
+    if (!b) {
+        set_error("bfm_batch_set_forms: NULL batch");
+        return BFM_EINVAL;
+    }
+    if (algo != BFM_ALGO_AUTO && algo != BFM_ALGO_HYBRID && algo != BFM_ALGO_MMA && algo != BFM_ALGO_SIMT) {
+        set_error("bfm_batch_set_forms: algo must be BFM_ALGO_AUTO, BFM_ALGO_HYBRID, BFM_ALGO_MMA or BFM_ALGO_SIMT");
+        return BFM_EINVAL;
+    }
+    if (b->ntiles_all > 0) {
+        set_error("bfm_batch_set_forms: tiles were already added");
+        return BFM_EINVAL;
+    }
+    b->forms = algo;
+    return BFM_OK;
+}
+
+int bfm_batch_tile_form(bfm_batch_t b, int tile_id) {
+    if (!b || tile_id < 0 || tile_id >= (int)b->tile_form.size()) return -1;
+    return b->tile_form[(size_t)tile_id];
 }
 
 }  // extern "C"

@@ -200,6 +200,21 @@ bfm_status launch_hybrid(const bfm_design_s* d, int dtype, const void* Y, const 
                          int n_hist, double h_frac, double lambda, int32_t* brk, float* mean, float* sigma,
                          float* beta, uint8_t* status, cudaStream_t stream, float* maxmo);
 cudaError_t hybrid_read_clear_errors(cudaStream_t s, unsigned int* bits);
+// Batched hybrid launch (bfm_batch): a group holds tiles of one kernel variant
+// (k, storage, mask) whose tables and rings fit one shared-memory layout, run
+// by one persistent kernel over 512-pixel work blocks.
+struct HybGroup;
+HybGroup* hyb_group_create(int k, int dtype, bool has_mask);
+void hyb_group_destroy(HybGroup* g);
+bool hyb_group_variant(const HybGroup* g, int k, int dtype, bool has_mask);
+// 1: appended; 0: the group's layout would no longer fit (nothing changed);
+// -1: the hybrid form does not take the tile (message set).
+int hyb_group_add(HybGroup* g, const bfm_design_s* d, const void* Y, const uint32_t* mask, int64_t m, int n_hist,
+                  double h_frac, double lambda, int32_t* brk, float* mean, float* sigma, float* beta,
+                  uint8_t* status);
+bfm_status hyb_group_upload(HybGroup* g);  // device tile table (again after adds)
+bfm_status hyb_group_node(HybGroup* g, cudaGraph_t graph, const cudaGraphNode_t* dep, cudaGraphNode_t* node);
+int64_t hyb_group_blocks(const HybGroup* g);
 
 // Bound of the staged forms' consumer-side stage waits (bfm_stage_wait_limit).
 uint64_t stage_wait_ns();

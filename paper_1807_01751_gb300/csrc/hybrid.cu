@@ -7,8 +7,8 @@
 // the SM's shared memory.  Warps 0..15 own 32 pixels each (the pixel's TMEM
 // lane is its thread's lane), warp 16 issues the 2-D TMA boxes of Y (128
 // pixels x 8 float or 16 int16 dates, one per M-tile and stage), warp 17
-// issues the tensor-core work and owns the tensor memory.  Per tile of 512
-// pixels (Section 2.1, Eq. 3-6, Algorithm 1 with missing values masked):
+// issues the tensor-core work and owns the tensor memory.  Per work block of
+// 512 pixels (Section 2.1, Eq. 3-6, Algorithm 1 with missing values masked):
 //
 //   A   history, 16 dates per chunk: each pixel thread writes its row of the
 //       chunk's A operands into TMEM -- the 0/1 validity mask as fp16 and the
@@ -38,18 +38,21 @@
 //
 // Precision: the Gram sums use the basis split into fp16 hi + lo (22 bits);
 // X'My uses tf32 y (beta0 is only the start of the refinement); r0 and the
-// coefficients are split hi + lo with per-pixel power-of-two scales, so the
-// fitted values carry ~22 bits of beta0 and of delta separately, as the
-// float rounding of an intercept or trend would otherwise enter every
-// residual of a window alike.
+// coefficients are split hi + lo with per-pixel power-of-two scales, and the
+// regressors of the fitted values, scaled by 2^12, three ways (hi, mid, lo),
+// so that the fitted values carry ~22 bits of beta0 and of delta separately
+// and lose no more to the regressors: the float rounding of an intercept or
+// trend would otherwise enter every residual of a window alike.
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstring>
 #include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "bfm_internal.cuh"
 #include "ptx.cuh"
@@ -135,6 +138,24 @@ struct HLayout {
     size_t gh, gl, xt, yh, stages, ring, bars, total;
 };
 
+// One tile of a batched launch (bfm_batch): its tensor map, parameters and
+// first 512-pixel work block within its group.
+struct HybBatchTile {
+    CUtensorMap tm;  // 64-byte aligned type
+    HybridParams P;
+    int64_t block0;
+};
+
+// The batch side of a launch: the group's tiles (device memory), its work
+// blocks and the shared-memory layout that holds the largest tables and ring
+// among them.
+struct HybBatch {
+    const HybBatchTile* tiles;
+    int ntiles;
+    int64_t blocks;
+    HLayout lo;
+};
+
 __host__ __device__ inline size_t up1024(size_t x) { return (x + 1023) & ~(size_t)1023; }
 
 // Shared memory: Gram table hi and lo and the tf32 regressor table over the
@@ -150,7 +171,7 @@ __host__ __device__ inline HLayout hyb_layout(int n, int npad, int hmax) {
     L.stages = up1024(L.yh + tab_yhat_bytes(npad));
     L.ring = L.stages + (size_t)kStages * kStageBytes;
     L.bars = L.ring + (size_t)hmax * kPx * 4;
-    L.total = L.bars + (size_t)(2 * kStages + 13) * 8 + 16;
+    L.total = L.bars + (size_t)(2 * kStages + 14) * 8 + 16;
     return L;
 }
 
@@ -404,17 +425,19 @@ __device__ __forceinline__ void mon_mixed8(const Obs<T, kMask>& ob, const T* st,
     }
 }
 
-template <int KH, typename T, bool kMask>
+// kBatch: the work blocks of several tiles (Bt; tmap and P are unused but for
+// P.wait_ns), the tables of a block's tile loaded by the MMA warp when its
+// previous block belonged to another tile; otherwise the blocks of one tile.
+template <int KH, typename T, bool kMask, bool kBatch>
 __global__ void __launch_bounds__(kThreads, 1)
-    hybrid_kernel(const __grid_constant__ CUtensorMap tmap, const HybridParams P) {
+    hybrid_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ HybridParams P,
+                  const HybBatch Bt) {
     using B = Basis<KH>;
     constexpr int K = B::K, NBR = B::NBR;
     constexpr int G = Dt<T>::G;         // dates per stage
     constexpr int SPC = 16 / G;         // stages per 16-date chunk
     extern __shared__ __align__(1024) unsigned char smem[];
-    const int n = P.n, N = P.N, hmax = P.hmax, npad = P.npad;
-    const int64_t m = P.m;
-    const HLayout Lo = hyb_layout(n, npad, hmax);
+    const HLayout Lo = kBatch ? Bt.lo : hyb_layout(P.n, P.npad, P.hmax);
     unsigned char* s_gh = smem + Lo.gh;
     unsigned char* s_gl = smem + Lo.gl;
     unsigned char* s_xt = smem + Lo.xt;
@@ -430,16 +453,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* yempty = yfull + 2;           // [2] fitted-value piece read by every pixel warp
     uint64_t* accd = yempty + 2;            // pass A sums complete
     uint64_t* cdone = accd + 1;             // refinement sums complete
-    uint64_t* coefb = cdone + 1;            // coefficient operands written (two uses per tile)
-    uint64_t* dminb = coefb + 1;            // earliest window start of the tile published
+    uint64_t* coefb = cdone + 1;            // coefficient operands written (two uses per block)
+    uint64_t* dminb = coefb + 1;            // earliest window start of the block published
     uint64_t* finb = dminb + 1;             // the MMA warp's last MMAs done
-    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(finb + 1);
-    int* s_dstart = reinterpret_cast<int*>(s_tmem + 1);  // [2], by tile parity
+    uint64_t* tabb = finb + 1;              // batch: earlier MMAs done / a tile's tables landed
+    uint32_t* s_tmem = reinterpret_cast<uint32_t*>(tabb + 1);
+    int* s_dstart = reinterpret_cast<int*>(s_tmem + 1);  // [2], by block parity
     volatile uint32_t* abort_flag = s_tmem + 3;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    {
-        const size_t nh16 = (size_t)((n + 15) & ~15);
+    if constexpr (!kBatch) {
+        const int npad = P.npad;
+        const size_t nh16 = (size_t)((P.n + 15) & ~15);
         auto copy = [&](unsigned char* dst, size_t src_off, size_t bytes) {
             const uint4* s = reinterpret_cast<const uint4*>(P.tabs + src_off);
             uint4* d = reinterpret_cast<uint4*>(dst);
@@ -466,6 +491,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         ptx::mbar_init(coefb, kCons);
         ptx::mbar_init(dminb, kCons);
         ptx::mbar_init(finb, 1);
+        ptx::mbar_init(tabb, 1);
         s_dstart[0] = INT_MAX;
         s_dstart[1] = INT_MAX;
         *abort_flag = 0u;
@@ -478,10 +504,32 @@ __global__ void __launch_bounds__(kThreads, 1)
     ptx::tc_fence_after();
     const uint32_t tmem = *s_tmem;
 
-    const int64_t ntiles = (m + kPx - 1) / kPx;
-    const int nst_h = (n + G - 1) / G;   // stages of one history pass
-    const int nck = (n + 15) / 16;       // 16-date chunks of the history
-    auto dstart_of = [&](int v) -> int {
+    // 512-pixel work blocks; the tile of block wb and the block's first pixel in it
+    const int64_t nwork = kBatch ? Bt.blocks : (P.m + kPx - 1) / kPx;
+    auto locate = [&](int64_t wb, int& ti, int64_t& px0) {
+        if constexpr (kBatch) {
+            int lo = 0, hi = Bt.ntiles - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (Bt.tiles[mid].block0 <= wb)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            ti = lo;
+            px0 = (wb - Bt.tiles[lo].block0) * kPx;
+        } else {
+            ti = 0;
+            px0 = wb * kPx;
+        }
+    };
+    auto params = [&](int ti) -> const HybridParams& {
+        if constexpr (kBatch)
+            return Bt.tiles[ti].P;
+        else
+            return P;
+    };
+    auto dstart_of = [](int v, int n) -> int {
         const int d = v < n ? v : n;
         return d / G * G;
     };
@@ -489,12 +537,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == kProdWarp) {
         // ---------------- TMA producer: passes A, B' over the history, C from the window start
         if (lane == 0) {
-            ptx::prefetch_tmap(&tmap);
+            if constexpr (!kBatch) ptx::prefetch_tmap(&tmap);
             const uint64_t keep = l2_evict_last(), normal = l2_evict_normal(), drop = l2_evict_first();
             int64_t js = 0;
             bool ok = true;
             uint32_t dpar = 0;
-            auto issue = [&](int64_t px0, int d0, uint64_t pol) -> bool {
+            auto issue = [&](const CUtensorMap* tm, int64_t px0, int d0, uint64_t pol) -> bool {
                 const int slot = (int)(js % kStages);
                 if (js >= kStages &&
                     !wait_released(empty + slot, (uint32_t)(((js / kStages) - 1) & 1), abort_flag, kWaitNs)) {
@@ -505,23 +553,33 @@ __global__ void __launch_bounds__(kThreads, 1)
                 unsigned char* dst = stages + slot * kStageBytes;
                 ptx::mbar_arrive_expect_tx(full + slot, (uint32_t)kStageBytes);
 #pragma unroll
-                for (int g = 0; g < kMT; ++g) tma_box(dst + g * kBoxBytes, &tmap, full + slot, (int)(px0 + g * kBoxPx), d0, pol);
+                for (int g = 0; g < kMT; ++g) tma_box(dst + g * kBoxBytes, tm, full + slot, (int)(px0 + g * kBoxPx), d0, pol);
                 ++js;
                 return true;
             };
-            int it = 0;
-            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
-                const int64_t px0 = tile * kPx;
-                for (int s = 0; s < nst_h && ok; ++s) ok = issue(px0, s * G, keep);
-                for (int s = 0; s < nst_h && ok; ++s) ok = issue(px0, s * G, drop);
+            int it = 0, cur = -1;
+            for (int64_t wb = blockIdx.x; wb < nwork && ok; wb += gridDim.x, ++it) {
+                int ti;
+                int64_t px0;
+                locate(wb, ti, px0);
+                const CUtensorMap* tm = &tmap;
+                if constexpr (kBatch) {
+                    tm = &Bt.tiles[ti].tm;
+                    if (ti != cur) ptx::fence_tmap_acquire(tm);  // a map in global memory
+                    cur = ti;
+                }
+                const int n = params(ti).n, N = params(ti).N;
+                const int nst_h = (n + G - 1) / G;  // stages of one history pass
+                for (int s = 0; s < nst_h && ok; ++s) ok = issue(tm, px0, s * G, keep);
+                for (int s = 0; s < nst_h && ok; ++s) ok = issue(tm, px0, s * G, drop);
                 if (!ok) break;
                 if (!wait_bar(dminb, dpar, abort_flag, kWaitNs)) {
                     raise_abort(abort_flag);
                     break;
                 }
                 dpar ^= 1u;
-                const int ds = dstart_of(s_dstart[it & 1]);
-                for (int d0 = ds; d0 < N && ok; d0 += G) ok = issue(px0, d0, normal);
+                const int ds = dstart_of(s_dstart[it & 1], n);
+                for (int d0 = ds; d0 < N && ok; d0 += G) ok = issue(tm, px0, d0, normal);
             }
             // copies still in flight land before the CTA's shared memory is released
             for (int64_t i = js > kStages ? js - kStages : 0; i < js; ++i)
@@ -569,8 +627,39 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ptx::tc_fence_after();
                 return true;
             };
-            int it = 0;
-            for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++it) {
+            int it = 0, cur = -1;
+            uint32_t tpar = 0;
+            bool tab_pending = false;  // a table copy not seen to land
+            for (int64_t wb = blockIdx.x; wb < nwork && ok; wb += gridDim.x, ++it) {
+                int ti;
+                int64_t px0;
+                locate(wb, ti, px0);
+                const HybridParams& Q = params(ti);
+                const int n = Q.n, N = Q.N;
+                const int nck = (n + 15) / 16;  // 16-date chunks of the history
+                if constexpr (kBatch) {
+                    if (ti != cur) {
+                        // the MMAs of the previous tile have read its tables before they are replaced
+                        if (cur >= 0) {
+                            ptx::mma_commit(tabb);
+                            if (!(ok = wait_bar(tabb, tpar, abort_flag, kWaitNs))) break;
+                            tpar ^= 1u;
+                        }
+                        const int npad = Q.npad;
+                        const uint32_t bg = (uint32_t)((n + 15) & ~15) / 8 * 384, bx = (uint32_t)((n + 15) & ~15) / 4 * 256;
+                        const uint32_t by = (uint32_t)tab_yhat_bytes(npad);
+                        ptx::mbar_arrive_expect_tx(tabb, 2 * bg + bx + by);
+                        ptx::bulk_g2s(s_gh, Q.tabs, bg, tabb);
+                        ptx::bulk_g2s(s_gl, Q.tabs + tab_gram_lo(npad), bg, tabb);
+                        ptx::bulk_g2s(s_xt, Q.tabs + tab_x(npad), bx, tabb);
+                        ptx::bulk_g2s(s_yh, Q.tabs + tab_yhat(npad), by, tabb);
+                        tab_pending = true;
+                        if (!(ok = wait_bar(tabb, tpar, abort_flag, kWaitNs))) break;
+                        tab_pending = false;
+                        tpar ^= 1u;
+                        cur = ti;
+                    }
+                }
                 // pass A: masked basis sums and X'My
                 for (int c = 0; c < nck && ok; ++c) {
                     if (!(ok = wait_a())) break;
@@ -616,14 +705,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 if (!ok) break;
                 ptx::mma_commit(cdone);
-                // pass C: fitted values of beta0 + delta from the tile's earliest window start
+                // pass C: fitted values of beta0 + delta from the block's earliest window start
                 if (!(ok = wait_bar(coefb, cpar, abort_flag, kWaitNs))) break;
                 cpar ^= 1u;
                 ptx::tc_fence_after();
-                const int ds = dstart_of(s_dstart[it & 1]);
+                const int ds = dstart_of(s_dstart[it & 1], n);
                 for (int d0 = ds; d0 < N && ok; d0 += 32) ok = piece(d0, true);
             }
             if (!ok) raise_abort(abort_flag);
+            // a table copy in flight lands before the CTA's shared memory is released
+            if (tab_pending) ptx::mbar_wait_bounded(tabb, tpar, kWaitNs);
             // every MMA issued has completed before the tensor memory is released
             ptx::mma_commit(finb);
             ptx::mbar_wait_bounded(finb, 0u, kWaitNs);
@@ -632,7 +723,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         // ---------------- pixel warps
         const int w = warp, g = w >> 2, q = w & 3;
-        const int pl = 32 * w + lane;                       // pixel within the tile
+        const int pl = 32 * w + lane;                       // pixel within the block
         const uint32_t tl = (uint32_t)(32 * q) << 16;       // TMEM lane field of this warp
         const uint32_t tcol = tmem + 128u * (uint32_t)g;    // this M-tile's columns
         float* ring_t = ring + pl;
@@ -642,9 +733,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         int cslot = 0;
         uint32_t cphase = 0;
         uint32_t cc = 0, pc = 0, accpar = 0, cdpar = 0, dpar = 0;
-        // Wait for the next stage: this thread's column in it, or nullptr (warp-uniform)
-        // when the wait gave up or the CTA is aborting; a warp that gives up neither
-        // reads nor releases the stage.
         // Wait for the next stage: this thread's column in it, or nullptr (warp-uniform)
         // when the wait gave up or the CTA is aborting; a warp that gives up neither
         // reads nor releases the stage.  Fast path: one look at the barrier.  A bound
@@ -687,22 +775,29 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(bar);
         };
-        auto write_unfitted = [&](int64_t p, int st) {
-            P.brk[p] = -1;
-            P.mean[p] = qnan;
-            P.sigma[p] = qnan;
+        auto write_unfitted = [&](const HybridParams& Q, int64_t p, int st) {
+            Q.brk[p] = -1;
+            Q.mean[p] = qnan;
+            Q.sigma[p] = qnan;
 #pragma unroll
-            for (int a = 0; a < K; ++a) P.beta[(size_t)a * m + p] = qnan;
-            P.status[p] = (uint8_t)st;
-            if (P.maxmo) P.maxmo[p] = qnan;
+            for (int a = 0; a < K; ++a) Q.beta[(size_t)a * Q.m + p] = qnan;
+            Q.status[p] = (uint8_t)st;
+            if (Q.maxmo) Q.maxmo[p] = qnan;
         };
 
         int it = 0;
-        int64_t tile = blockIdx.x;
-        for (; tile < ntiles; tile += gridDim.x, ++it) {
-            const int64_t p = tile * kPx + pl;
+        int64_t wb = blockIdx.x;
+        for (; wb < nwork; wb += gridDim.x, ++it) {
+            int ti;
+            int64_t px0;
+            locate(wb, ti, px0);
+            const HybridParams& Q = params(ti);
+            const int n = Q.n, N = Q.N, hmax = Q.hmax;
+            const int nck = (n + 15) / 16;  // 16-date chunks of the history
+            const int64_t m = Q.m;
+            const int64_t p = px0 + pl;
             const bool active = p < m;
-            Obs<T, kMask> ob{kMask ? P.mask + (active ? (p >> 5) : 0) : nullptr, (size_t)P.mask_words,
+            Obs<T, kMask> ob{kMask ? Q.mask + (active ? (p >> 5) : 0) : nullptr, (size_t)Q.mask_words,
                              1u << (p & 31)};
 
             // ---- pass A: A operands of the masked basis sums and X'My
@@ -795,7 +890,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 arrive(coefb);
             }
             const bool fit = np > K && nonsingular;
-            int hp = (int)floor(P.h_frac * (double)np);
+            int hp = (int)floor(Q.h_frac * (double)np);
             hp = hp < 1 ? 1 : (hp > np ? np : hp);
             if (!fit) hp = 1;  // keeps the ring arithmetic in range; nothing of it is used
             hp = hp > hmax ? hmax : hp;  // n_p <= n_hist, so this never binds: the ring holds hmax slots
@@ -883,19 +978,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             // outputs known now (the rest after the monitoring scan)
             if (active) {
                 if (np <= K) {
-                    write_unfitted(p, BFM_PX_INSUFFICIENT_HISTORY);
+                    write_unfitted(Q, p, BFM_PX_INSUFFICIENT_HISTORY);
                 } else if (!nonsingular) {
-                    write_unfitted(p, BFM_PX_SINGULAR);
+                    write_unfitted(Q, p, BFM_PX_SINGULAR);
                 } else {
-                    P.sigma[p] = sig;
+                    Q.sigma[p] = sig;
                     // beta of the centred trend -> raw parameterisation of Eq. 2
                     float bt[K];
 #pragma unroll
                     for (int a = 0; a < K; ++a) bt[a] = b0[a] + dl[a];
-                    P.beta[p] = fmaf(-bt[1], P.c_over_s, bt[0]);
-                    P.beta[(size_t)m + p] = bt[1] * P.inv_s;
+                    Q.beta[p] = fmaf(-bt[1], Q.c_over_s, bt[0]);
+                    Q.beta[(size_t)m + p] = bt[1] * Q.inv_s;
 #pragma unroll
-                    for (int a = 2; a < K; ++a) P.beta[(size_t)a * m + p] = bt[a];
+                    for (int a = 2; a < K; ++a) Q.beta[(size_t)a * m + p] = bt[a];
                 }
             }
             {
@@ -907,7 +1002,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 coef_words<K>(dfin, s_b, wv, rep);
                 coef_store(tl + tcol + kColDl, wv);
             }
-            // the tile's earliest window start, for the producer and the MMA warp
+            // the block's earliest window start, for the producer and the MMA warp
             {
                 const unsigned v = active ? (unsigned)wdate : (unsigned)n;
                 const unsigned wmn = __reduce_min_sync(~0u, v);
@@ -922,13 +1017,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (!wait_w(dminb, dpar)) break;
             dpar ^= 1u;
-            const int ds = dstart_of(s_dstart[it & 1]);
+            const int ds = dstart_of(s_dstart[it & 1], n);
             if (tid == 0) s_dstart[(it + 1) & 1] = INT_MAX;
 
             // ---- pass C: window fill from the history, then the monitoring scan
             const float inv_scale = (fit && !degenerate) ? 1.f / (sig * sqrtf((float)np)) : 0.f;
             const float inv2 = inv_scale * inv_scale;
-            const float lam2ln2 = P.lam2 * kLn2f, blg = lam2ln2 * log2_fast((float)np);
+            const float lam2 = Q.lam2, lam2ln2 = lam2 * kLn2f, blg = lam2ln2 * log2_fast((float)np);
+            float* const maxmo = Q.maxmo;
             const float jlimf = (float)floor(kEuler * (double)np);  // J / n_p <= e  <=>  J <= jlim
             Mon mo{};
             mo.hp_off = hp * kPx;
@@ -964,12 +1060,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     mo.blk = 0.f;
                     mo.amax = 0.f;
                     if (d8 >= n && d8 + 8 <= N) {
-                        if (P.maxmo)
+                        if (maxmo)
                             mon8<true, true>(ob, st8, d8, N, yh, ring_t, mo, Wu);
                         else
                             mon8<true, false>(ob, st8, d8, N, yh, ring_t, mo, Wu);
                     } else {
-                        mon_mixed8(ob, st8, d8, n, N, yh, ring_t, mo, Wu, P.maxmo != nullptr);
+                        mon_mixed8(ob, st8, d8, n, N, yh, ring_t, mo, Wu, maxmo != nullptr);
                     }
                     comp_add(sh, sl, mo.blk);
                     // the boundary grows with the position: a stretch whose largest |MO| stays
@@ -977,14 +1073,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // 1e-6 relative, so that rounding of the boundary never hides a crossing)
                     if (brk < 0) {
                         const float Jf0 = (float)J0;
-                        const float b2f = (Jf0 > jlimf ? fmaf(lam2ln2, log2_fast(Jf0), -blg) : P.lam2) * 0.999999f;
+                        const float b2f = (Jf0 > jlimf ? fmaf(lam2ln2, log2_fast(Jf0), -blg) : lam2) * 0.999999f;
                         if (fmaf(mo.amax * mo.amax, inv2, -b2f) > 0.f) {
                             float Jc = Jf0;
 #pragma unroll
                             for (int u = 0; u < 8; ++u) {
                                 const int d = d8 + u;
                                 if (d >= n && ob.valid(st8[u * kBoxPx], d, d < N)) {
-                                    const float b2 = Jc > jlimf ? fmaf(lam2ln2, log2_fast(Jc), -blg) : P.lam2;
+                                    const float b2 = Jc > jlimf ? fmaf(lam2ln2, log2_fast(Jc), -blg) : lam2;
                                     if (brk < 0 && fmaf(Wu[u] * Wu[u], inv2, -b2) > 0.f) brk = d;
                                     Jc += 1.f;
                                 }
@@ -1000,29 +1096,32 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int Np = np + mo.cnt;
             if (fit) {
                 if (degenerate) {
-                    P.status[p] = BFM_PX_DEGENERATE;
-                    P.brk[p] = -1;
-                    P.mean[p] = 0.f;
-                    if (P.maxmo) P.maxmo[p] = 0.f;
+                    Q.status[p] = BFM_PX_DEGENERATE;
+                    Q.brk[p] = -1;
+                    Q.mean[p] = 0.f;
+                    if (maxmo) maxmo[p] = 0.f;
                 } else if (Np == np) {
-                    P.status[p] = BFM_PX_NO_MONITOR;
-                    P.brk[p] = -1;
-                    P.mean[p] = qnan;
-                    if (P.maxmo) P.maxmo[p] = qnan;
+                    Q.status[p] = BFM_PX_NO_MONITOR;
+                    Q.brk[p] = -1;
+                    Q.mean[p] = qnan;
+                    if (maxmo) maxmo[p] = qnan;
                 } else {
-                    P.status[p] = BFM_PX_OK;
-                    P.brk[p] = brk;
-                    P.mean[p] = (sh + sl) * inv_scale / (float)(Np - np);
+                    Q.status[p] = BFM_PX_OK;
+                    Q.brk[p] = brk;
+                    Q.mean[p] = (sh + sl) * inv_scale / (float)(Np - np);
                     // largest |MO| (positive on an exact tie of opposite signs)
-                    if (P.maxmo) P.maxmo[p] = (mo.wmax >= -mo.wmin ? mo.wmax : mo.wmin) * inv_scale;
+                    if (maxmo) maxmo[p] = (mo.wmax >= -mo.wmin ? mo.wmax : mo.wmin) * inv_scale;
                 }
             }
         }
         if (bad) {
             // a wait gave up: mark this thread's unfinished pixels
-            for (; tile < ntiles; tile += gridDim.x) {
-                const int64_t p = tile * kPx + pl;
-                if (p < m) write_unfitted(p, BFM_PX_TIMEOUT);
+            for (; wb < nwork; wb += gridDim.x) {
+                int ti;
+                int64_t px0;
+                locate(wb, ti, px0);
+                const HybridParams& Q = params(ti);
+                if (px0 + pl < Q.m) write_unfitted(Q, px0 + pl, BFM_PX_TIMEOUT);
             }
         }
     }
@@ -1036,10 +1135,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 template <int KH, typename T, bool kMask>
 bfm_status launch_one(const CUtensorMap& tm, const HybridParams& P, int grid, size_t smem, cudaStream_t st) {
-    auto* fn = hybrid_kernel<KH, T, kMask>;
+    auto* fn = hybrid_kernel<KH, T, kMask, false>;
     const cudaError_t ea = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (ea != cudaSuccess) return cuda_fail(ea, "bfm_monitor (hybrid): shared memory attribute");
-    fn<<<grid, kThreads, smem, st>>>(tm, P);
+    fn<<<grid, kThreads, smem, st>>>(tm, P, HybBatch{});
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "bfm_monitor (hybrid): launch");
     return BFM_OK;
@@ -1126,19 +1225,23 @@ bool hybrid_supported(const bfm_design_s* d, int dtype, int n_hist, double h_fra
     return hyb_layout(n_hist, hyb_npad(d->N), hyb_hmax(n_hist, h_frac)).total <= kSmemCap;
 }
 
-bfm_status launch_hybrid(const bfm_design_s* d, int dtype, const void* Y, const uint32_t* mask, int64_t m,
-                         int n_hist, double h_frac, double lambda, int32_t* brk, float* mean, float* sigma,
-                         float* beta, uint8_t* status, cudaStream_t stream, float* maxmo) {
+namespace {
+
+// Parameters and tensor map of one tile (false, with a message, when the
+// hybrid form does not take it).
+bool hyb_fill(const bfm_design_s* d, int dtype, const void* Y, const uint32_t* mask, int64_t m, int n_hist,
+              double h_frac, double lambda, int32_t* brk, float* mean, float* sigma, float* beta, uint8_t* status,
+              float* maxmo, HybridParams* Pout, CUtensorMap* tm) {
     if (!hybrid_supported(d, dtype, n_hist, h_frac, Y, m)) {
-        set_error("bfm_monitor: the hybrid form needs Y with a 16-byte aligned base and rows of a multiple of "
-                  "16 bytes, and basis tables, stages and a residual ring of floor(h_frac * n_hist) slots for "
-                  "512 pixels within the shared memory of one SM");
-        return BFM_EUNSUPPORTED;
+        set_error("the hybrid form needs Y with a 16-byte aligned base and rows of a multiple of 16 bytes, and "
+                  "basis tables, stages and a residual ring of floor(h_frac * n_hist) slots for 512 pixels within "
+                  "the shared memory of one SM");
+        return false;
     }
     auto enc = encode_tiled();
     if (!enc) {
-        set_error("bfm_monitor (hybrid): cuTensorMapEncodeTiled is not available");
-        return BFM_ECUDA;
+        set_error("hybrid form: cuTensorMapEncodeTiled is not available");
+        return false;
     }
     const size_t elt = dtype == BFM_F32 ? 4 : 2;
     HybridParams P{};
@@ -1161,23 +1264,39 @@ bfm_status launch_hybrid(const bfm_design_s* d, int dtype, const void* Y, const 
     P.beta = beta;
     P.status = status;
     P.maxmo = maxmo;
-    CUtensorMap tm;
-    std::memset(&tm, 0, sizeof tm);
+    std::memset(tm, 0, sizeof *tm);
     const int G = dtype == BFM_F32 ? Dt<float>::G : Dt<int16_t>::G;
     const cuuint64_t gdim[2] = {(cuuint64_t)m, (cuuint64_t)d->N};
     const cuuint64_t gstride[1] = {(cuuint64_t)m * elt};
     const cuuint32_t box[2] = {(cuuint32_t)kBoxPx, (cuuint32_t)G};
     const cuuint32_t es[2] = {1u, 1u};
-    if (enc(&tm, elt == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 2,
+    if (enc(tm, elt == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16, 2,
             const_cast<void*>(Y), gdim, gstride, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
-        set_error("bfm_monitor (hybrid): cuTensorMapEncodeTiled failed for Y");
-        return BFM_ECUDA;
+        set_error("hybrid form: cuTensorMapEncodeTiled failed for Y");
+        return false;
     }
+    *Pout = P;
+    return true;
+}
+
+int sm_count_cur() {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
-    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return cuda_fail(e, "bfm_monitor (hybrid): device attributes");
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    return sms;
+}
+
+}  // namespace
+
+bfm_status launch_hybrid(const bfm_design_s* d, int dtype, const void* Y, const uint32_t* mask, int64_t m,
+                         int n_hist, double h_frac, double lambda, int32_t* brk, float* mean, float* sigma,
+                         float* beta, uint8_t* status, cudaStream_t stream, float* maxmo) {
+    HybridParams P;
+    CUtensorMap tm;
+    if (!hyb_fill(d, dtype, Y, mask, m, n_hist, h_frac, lambda, brk, mean, sigma, beta, status, maxmo, &P, &tm))
+        return BFM_EUNSUPPORTED;
+    const int sms = sm_count_cur();
     const int64_t ntiles = (m + kPx - 1) / kPx;
     const int grid = (int)(ntiles < (int64_t)sms ? ntiles : (int64_t)sms);
     const size_t smem = hyb_layout(n_hist, P.npad, P.hmax).total;
@@ -1185,5 +1304,118 @@ bfm_status launch_hybrid(const bfm_design_s* d, int dtype, const void* Y, const 
     if (d->k == 2) return launch_kh<2>(tm, P, dtype, grid, smem, stream);
     return launch_kh<3>(tm, P, dtype, grid, smem, stream);
 }
+
+// ---- batched launch (bfm_batch) --------------------------------------------------------------
+
+struct HybGroup {
+    int k, dtype;
+    bool mask;
+    int nmax = 0, npadmax = 0, hmaxmax = 0;  // the layout holds the largest of each
+    int64_t blocks = 0;
+    std::vector<HybBatchTile> tiles;
+    HybBatchTile* d_tiles = nullptr;
+    bool dirty = true;
+};
+
+HybGroup* hyb_group_create(int k, int dtype, bool has_mask) {
+    auto* g = new HybGroup;
+    g->k = k;
+    g->dtype = dtype;
+    g->mask = has_mask;
+    return g;
+}
+
+void hyb_group_destroy(HybGroup* g) {
+    if (!g) return;
+    if (g->d_tiles) cudaFree(g->d_tiles);
+    delete g;
+}
+
+bool hyb_group_variant(const HybGroup* g, int k, int dtype, bool has_mask) {
+    return g->k == k && g->dtype == dtype && g->mask == has_mask;
+}
+
+int hyb_group_add(HybGroup* g, const bfm_design_s* d, const void* Y, const uint32_t* mask, int64_t m, int n_hist,
+                  double h_frac, double lambda, int32_t* brk, float* mean, float* sigma, float* beta,
+                  uint8_t* status) {
+    HybBatchTile t;
+    if (!hyb_fill(d, g->dtype, Y, mask, m, n_hist, h_frac, lambda, brk, mean, sigma, beta, status, nullptr, &t.P,
+                  &t.tm))
+        return -1;
+    const int nmax = std::max(g->nmax, n_hist), npadmax = std::max(g->npadmax, t.P.npad),
+              hmaxmax = std::max(g->hmaxmax, t.P.hmax);
+    if (hyb_layout(nmax, npadmax, hmaxmax).total > kSmemCap) return 0;
+    g->nmax = nmax;
+    g->npadmax = npadmax;
+    g->hmaxmax = hmaxmax;
+    t.block0 = g->blocks;
+    g->blocks += (m + kPx - 1) / kPx;
+    g->tiles.push_back(t);
+    g->dirty = true;
+    return 1;
+}
+
+bfm_status hyb_group_upload(HybGroup* g) {
+    if (!g->dirty) return BFM_OK;
+    if (g->d_tiles) cudaFree(g->d_tiles);
+    g->d_tiles = nullptr;
+    cudaError_t e = cudaMalloc(&g->d_tiles, sizeof(HybBatchTile) * g->tiles.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(g->d_tiles, g->tiles.data(), sizeof(HybBatchTile) * g->tiles.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "bfm_batch: uploading hybrid tile descriptors");
+    g->dirty = false;
+    return BFM_OK;
+}
+
+namespace {
+template <int KH, typename T, bool kMask>
+void* hyb_batch_fn() {
+    return (void*)hybrid_kernel<KH, T, kMask, true>;
+}
+}  // namespace
+
+bfm_status hyb_group_node(HybGroup* g, cudaGraph_t graph, const cudaGraphNode_t* dep, cudaGraphNode_t* node) {
+    void* fn = nullptr;
+    const bool f32 = g->dtype == BFM_F32;
+    switch (g->k) {
+        case 1:
+            fn = f32 ? (g->mask ? hyb_batch_fn<1, float, true>() : hyb_batch_fn<1, float, false>())
+                     : (g->mask ? hyb_batch_fn<1, int16_t, true>() : hyb_batch_fn<1, int16_t, false>());
+            break;
+        case 2:
+            fn = f32 ? (g->mask ? hyb_batch_fn<2, float, true>() : hyb_batch_fn<2, float, false>())
+                     : (g->mask ? hyb_batch_fn<2, int16_t, true>() : hyb_batch_fn<2, int16_t, false>());
+            break;
+        default:
+            fn = f32 ? (g->mask ? hyb_batch_fn<3, float, true>() : hyb_batch_fn<3, float, false>())
+                     : (g->mask ? hyb_batch_fn<3, int16_t, true>() : hyb_batch_fn<3, int16_t, false>());
+            break;
+    }
+    HybBatch bt{};
+    bt.tiles = g->d_tiles;
+    bt.ntiles = (int)g->tiles.size();
+    bt.blocks = g->blocks;
+    bt.lo = hyb_layout(g->nmax, g->npadmax, g->hmaxmax);
+    const size_t smem = bt.lo.total;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "bfm_batch: hybrid kernel shared memory attribute");
+    // the single-tile parameters are unused but for the stage-wait bound
+    static CUtensorMap tm_unused;  // zero; never read by the batched kernel
+    HybridParams P{};
+    P.wait_ns = g->tiles.empty() ? stage_wait_ns() : g->tiles[0].P.wait_ns;
+    void* args[3] = {&tm_unused, &P, &bt};
+    const int sms = sm_count_cur();
+    cudaKernelNodeParams kp{};
+    kp.func = fn;
+    kp.gridDim = dim3((unsigned)std::min<int64_t>(g->blocks, sms));
+    kp.blockDim = dim3(kThreads);
+    kp.sharedMemBytes = (unsigned)smem;
+    kp.kernelParams = args;
+    e = cudaGraphAddKernelNode(node, graph, dep, dep ? 1 : 0, &kp);
+    if (e != cudaSuccess) return cuda_fail(e, "bfm_batch: hybrid kernel node");
+    return BFM_OK;
+}
+
+int64_t hyb_group_blocks(const HybGroup* g) { return g->blocks; }
 
 }  // namespace bfm

@@ -847,6 +847,8 @@ __global__ void __launch_bounds__(kThreads, 2) mma_batch_kernel(const MmaBatchTi
             else hi = mid - 1;
         }
         const MmaBatchTile* t = tiles + lo;
+        // the two threads that issue TMA loads (history passes, MOSUM pass)
+        if (threadIdx.x == 0 || threadIdx.x == kTile) ptx::fence_tmap_acquire(&t->tm);
         mma_block<KH, T, kMask>(&t->tm, t->P, blk - t->block0, smem, tmem);
     }
     ptx::tc_fence_before();

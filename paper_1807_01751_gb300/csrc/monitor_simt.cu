@@ -272,6 +272,7 @@ __global__ void __launch_bounds__(kNW * 32) batch_kernel(const BatchTileDesc* __
             const MonitorParams P = T.P;
             const long long block = it - T.block0;
             const CUtensorMap* tm = T.has_tma ? tmaps + lo : nullptr;
+            if (tm && threadIdx.x == 0) ptx::fence_tmap_acquire(tm);  // the TMA-issuing thread
             const int sel = (T.kh - 1) * 4 + (T.dtype == BFM_I16 ? 2 : 0) + (T.has_mask ? 1 : 0);
             switch (sel) {
                 case 0: simt_block<1, float, false>(tm, P, block, smem_raw, bar, uses); break;

@@ -86,6 +86,27 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// A tensor map in global memory (written by a host copy or by an earlier
+// kernel, possibly at an address that held another map before) is seen by
+// the TMA unit through the tensormap proxy, which may hold a cached copy:
+// this acquire fence orders the generic writes of the 128-byte map before the
+// calling thread's later TMA uses of it.  Maps passed as __grid_constant__
+// kernel parameters need none.
+__device__ __forceinline__ void fence_tmap_acquire(const CUtensorMap* map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+                 : "memory");
+}
+
+// Bulk copy without a tensor map: `bytes` (a multiple of 16) from global
+// memory at src to shared memory at dst (both 16-byte aligned), completing
+// that many bytes of transactions on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 // 2-D tiled TMA load: box at (x = innermost, y) of `map` into shared memory,
 // completing `bytes` of transactions on `bar`.
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {

@@ -60,22 +60,31 @@ def test_batch_equals_single_calls_and_oracle(bfm):
     b.close()
 
 
+def _mask_bits(rng, N, m, p_keep=0.85):
+    words = (m + 31) // 32
+    keep = rng.random((N, words * 32)) < p_keep
+    bits = np.zeros((N, words), np.uint32)
+    for b in range(32):
+        bits |= keep[:, b::32].astype(np.uint32) << np.uint32(b)
+    return torch.from_numpy(bits.view(np.int32)).cuda()
+
+
 def test_batch_tensor_core_variants(bfm):
     """Tiles of every harmonic order in both storage types, widths rounded to
-    multiples of 8 so that the batch gives them the tensor-core form: the
-    persistent tensor-core kernels (one per variant) reproduce single calls
-    bit for bit."""
+    multiples of 8, in a batch limited to the tensor-core form: the persistent
+    tensor-core kernels (one per variant) reproduce single calls bit for bit."""
     tiles = _tiles(scale=0.02, count=16, px_multiple=8)
-    b = bfm.Batch()
+    b = bfm.Batch(forms=bfm.BFM_ALGO_MMA)
     outs, singles, forms = [], [], set()
-    for t in tiles:
+    for i, t in enumerate(tiles):
         d = bfm.Design(t["dates"], t["k"], 23.0)
         Yd = torch.from_numpy(t["Y"]).cuda()
         dt = bfm.BFM_F32 if t["Y"].dtype == np.float32 else bfm.BFM_I16
-        form = bfm.bfm_batch_form(d, dt, t["n_hist"], 0.25, Yd, t["m"])
+        outs.append(b.add(d, Yd, n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"]))
+        form = b.form(i)
+        assert form in (bfm.BFM_ALGO_MMA, bfm.BFM_ALGO_SIMT)
         if form == bfm.BFM_ALGO_MMA:
             forms.add((t["k"], dt))
-        outs.append(b.add(d, Yd, n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"]))
         singles.append(bfm.monitor(d, Yd, n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"], algo=form))
     assert len(forms) >= 4, forms
     b.run()
@@ -87,6 +96,86 @@ def test_batch_tensor_core_variants(bfm):
         for key in a:
             np.testing.assert_array_equal(a[key].view(np.uint8), c[key].view(np.uint8))
     b.close()
+
+
+def test_batch_hybrid_variants(bfm):
+    """Tiles of every harmonic order in both storage types, some with mask
+    bits, in a batch of the default forms: the hybrid form takes the tiles
+    whose tables and ring fit one SM; its persistent kernels (one per variant
+    and layout group, tables reloaded where a CTA's next block belongs to
+    another tile) reproduce single calls bit for bit, on two replays."""
+    tiles = _tiles(scale=0.02, count=16, px_multiple=8)
+    rng = np.random.default_rng(11)
+    b = bfm.Batch()
+    outs, singles, forms = [], [], {}
+    for i, t in enumerate(tiles):
+        d = bfm.Design(t["dates"], t["k"], 23.0)
+        Yd = torch.from_numpy(t["Y"]).cuda()
+        dt = bfm.BFM_F32 if t["Y"].dtype == np.float32 else bfm.BFM_I16
+        mb = _mask_bits(rng, t["N"], t["m"]) if i % 4 == 1 else None
+        outs.append(b.add(d, Yd, n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"], mask_bits=mb))
+        form = b.form(i)
+        assert form == bfm.bfm_batch_form(d, dt, t["n_hist"], 0.25, Yd, t["m"])
+        v = (t["k"], dt, mb is not None)
+        forms[v] = forms.get(v, 0) + (form == bfm.BFM_ALGO_HYBRID)
+        singles.append(bfm.monitor(d, Yd, n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"], mask_bits=mb, algo=form))
+    assert sum(1 for v in forms.values() if v) >= 4, forms
+    b.run()
+    b.run()
+    torch.cuda.synchronize()
+    assert bfm.bfm_device_errors() == 0
+    for i, (o, sgl) in enumerate(zip(outs, singles)):
+        a, c = to_numpy(o), to_numpy(sgl)
+        for key in a:
+            np.testing.assert_array_equal(a[key].view(np.uint8), c[key].view(np.uint8), err_msg=f"tile {i} {key}")
+    b.close()
+
+
+def test_batch_forms_api(bfm):
+    """bfm_batch_set_forms takes AUTO, HYBRID, MMA or SIMT before the first
+    tile only; bfm_batch_tile_form answers -1 for an unknown id."""
+    b = bfm.Batch()
+    with pytest.raises(bfm.BfmError):
+        bfm.bfm_batch_set_forms(b.handle, bfm.BFM_ALGO_STREAM)
+    bfm.bfm_batch_set_forms(b.handle, bfm.BFM_ALGO_SIMT)
+    t = _tiles(count=1)[0]
+    d = bfm.Design(t["dates"], t["k"], 23.0)
+    b.add(d, torch.from_numpy(t["Y"]).cuda(), n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"])
+    assert b.form(0) == bfm.BFM_ALGO_SIMT
+    assert bfm.bfm_batch_tile_form(b.handle, 1) == -1
+    with pytest.raises(bfm.BfmError):
+        bfm.bfm_batch_set_forms(b.handle, bfm.BFM_ALGO_AUTO)
+    b.close()
+
+
+def test_batch_descriptors_at_reused_addresses(bfm):
+    """Batches created and destroyed in turn, over different tile sets: each
+    batch's tensor maps land in device memory that earlier batches' maps
+    occupied, and the TMA unit must not use a stale copy of a map at a reused
+    address.  Every batch reproduces single calls bit for bit."""
+    sets = []
+    for tiles in (_tiles(scale=0.02, count=8, px_multiple=8), _tiles(scale=0.01, count=8)):
+        row = []
+        for t in tiles:
+            d = bfm.Design(t["dates"], t["k"], 23.0)
+            row.append((d, torch.from_numpy(t["Y"]).cuda(), t))
+        sets.append(row)
+    refs = {}  # (set, tile, form) -> single-call outputs
+    for it in range(8):
+        si, forms = it % 2, (bfm.BFM_ALGO_AUTO, bfm.BFM_ALGO_MMA)[(it // 2) % 2]
+        b = bfm.Batch(forms=forms)
+        outs = [b.add(d, Yd, n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"]) for d, Yd, t in sets[si]]
+        b.run()
+        torch.cuda.synchronize()
+        assert bfm.bfm_device_errors() == 0
+        for i, (o, (d, Yd, t)) in enumerate(zip(outs, sets[si])):
+            key = (si, i, b.form(i))
+            if key not in refs:
+                refs[key] = to_numpy(bfm.monitor(d, Yd, n_hist=t["n_hist"], h_frac=0.25, lam=t["lam"], algo=key[2]))
+            a = to_numpy(o)
+            for k in a:
+                np.testing.assert_array_equal(a[k].view(np.uint8), refs[key][k].view(np.uint8), err_msg=f"{it} {i} {k}")
+        b.close()
 
 
 def test_batch_graph_replay_and_autotune_keep_results(bfm):

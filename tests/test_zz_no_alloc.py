@@ -5,8 +5,9 @@ process whose memory is pre-reserved by its own pool, a latency-critical
 loop where cudaMalloc/cudaFree would synchronise the device) use this entry
 point; its tile table, tensor maps and work counter live in a fixed array
 inside the library.  Its outputs must equal those of the ordinary entry
-point (bfm_monitor, CUDA-core form) on every tile, on two calls in a row
-that share and overwrite that array.  This file is collected last.
+point (bfm_monitor, CUDA-core form) on every tile, on calls in a row that
+share and overwrite that array (four calls, alternating two tile sets).
+This file is collected last.
 """
 import numpy as np
 import pytest
@@ -61,8 +62,10 @@ def _run_and_compare(bfm, tiles):
 def test_static_entry_matches_ordinary_entry_two_calls(bfm):
     first = _tiles(seed=7, count=12)
     second = _tiles(seed=8, count=5)   # fewer tiles: stale entries of the first call must not matter
-    _run_and_compare(bfm, first)
-    _run_and_compare(bfm, second)
+    # each call rewrites the tensor maps at the same addresses: alternating
+    # calls fail if the TMA unit used a cached copy of an earlier call's map
+    for tiles in (first, second, first, second):
+        _run_and_compare(bfm, tiles)
 
 
 def test_static_entry_rejects_too_many_tiles(bfm):
