@@ -481,6 +481,24 @@ def run_ours(args):
         torch.cuda.synchronize()
         link = {"h2d_gbs": 3 * (1 << 30) / (l0.elapsed_time(l1) / 1e3) / 1e9,
                 "how": "pinned host 1 GiB -> device, torch copy, 3 copies timed with CUDA events"}
+
+        def slice_rates(src):
+            # every 1 GiB slice of a pinned host buffer once: where its pages sit decides its rate
+            flat = src.view(torch.uint8).reshape(-1)
+            rates = []
+            for o in range(0, flat.numel(), 1 << 30):
+                n = min(1 << 30, flat.numel() - o)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                lb[:n].copy_(flat[o:o + n], non_blocking=True)
+                b.record(stream)
+                torch.cuda.synchronize()
+                rates.append(n / (a.elapsed_time(b) / 1e3) / 1e9)
+            return {"min_gbs": min(rates), "median_gbs": sorted(rates)[len(rates) // 2], "max_gbs": max(rates),
+                    "slices": len(rates)}
+
+        link["y_f32_buffer"] = slice_rates(Yh)
+        link["y_i16_buffer"] = slice_rates(Yh16)
         del lb
 
         def host_leg(Yhost, e_dt, e_elt):

@@ -187,13 +187,14 @@ int bfm_max_dates(void);
  * Cholesky pivot of its history Gram matrix, relative to the matching
  * diagonal entry, is below 1e-5.
  * Arithmetic: float arithmetic with one step of iterative refinement of the
- * least-squares solution, in the form BFM_ALGO_AUTO picks: the CUDA-core form
- * (float sums) or the tensor-core form (Gram, X'My, fitted values and the
- * refinement's X'r on fp16 tensor cores with hi/lo split operands, exact
- * power-of-two scales per pixel and FP32 accumulation).  Against an FP64
- * reference on well-conditioned pixels the CUDA-core form stays within 1e-5
- * and the tensor-core form within 1e-4 (1e-5 on float series of the
- * benchmark's recipe); the two forms differ in the last bits.
+ * least-squares solution, in the form BFM_ALGO_AUTO picks: the hybrid form
+ * (the masked sums, X'My, fitted values and the refinement's X'r on tensor
+ * cores, fp16 operands split hi/lo or three ways with exact power-of-two
+ * scales per pixel, tf32 y, FP32 accumulation; the scans on CUDA cores), the
+ * streaming or CUDA-core forms (float sums) or the tensor-core form.  Against
+ * an FP64 reference on well-conditioned pixels every form stays within 1e-5
+ * on float series (the tensor-core form within 1e-4 on int16 series); the
+ * forms differ in the last bits.
  * Errors: BFM_EINVAL, BFM_EUNSUPPORTED (N > bfm_max_dates()), BFM_ECUDA.
  */
 bfm_status bfm_monitor(bfm_design_t d, const void *Y, int dtype, const uint32_t *mask_bits, int64_t m,

@@ -221,8 +221,8 @@ uint64_t stage_wait_ns();
 void set_stage_wait_ns(uint64_t ns);
 
 // The form BFM_ALGO_AUTO takes for a single call, the host-buffer entry and
-// the server: the streaming form where it applies, else the tensor-core
-// form, else the CUDA-core form.
+// the server: the hybrid form where it applies, else the streaming form, else
+// the tensor-core form, else the CUDA-core form.
 int auto_form(const bfm_design_s* d, int dtype, int n_hist, double h_frac, const void* Y, int64_t m);
 bfm_status launch_complete(bfm_design_s* d, int dtype, const void* Y, const uint32_t* mask, int64_t m, int n_hist,
                            double h_frac, double lambda, int32_t* brk, float* mean, float* sigma, float* beta,

@@ -96,10 +96,13 @@ constexpr size_t kSmemCap = 232448;       // opt-in dynamic shared memory per bl
 // TMEM columns within an M-tile's 128 (the phases reuse them in turn):
 //   pass A : G sums [0, 32), X'My [32, 48), A buffers 2 x (mask 8 | y 16) [48, 96)
 //   pass B': c [0, 16), beta0 coefficients (24) [16, 40), r0 buffers 2 x (hi 8 | lo 8) [40, 72),
-//            fitted-value pieces 2 x 16 [72, 104)
+//            fitted-value pieces 2 x 16 [72, 104), the basis sums kept for the second solve [104, 128)
 //   pass C : beta0 coefficients [16, 40), delta coefficients (24) [40, 64), pieces 2 x 32 [64, 128)
 constexpr uint32_t kColG = 0, kColB = 32, kColA = 48, kColC = 0, kColB0 = 16, kColR = 40, kColY0 = 72, kColDl = 40,
                    kColY = 64;
+// Pass B' keeps the pixel's basis sums (up to 21) in [104, 128), free until pass C, for the
+// second solve, so that they do not occupy registers through the pass.
+constexpr uint32_t kColS = 104;
 // Coefficient operands: 24 columns per set, A_hi (K = 32: 16 columns) then A_lo (K = 16: 8 columns).
 constexpr uint32_t kCoefLo = 16;
 // The regressors of the fitted-value table are scaled by 2^12 before their three-way fp16 split.
@@ -850,6 +853,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int a = 0; a < K; ++a) Bv[a] = v16[a] + v16[8 + a];
             }
             const int np = (int)S[0];  // basis row 0 is 1: the count of valid history dates
+            {
+                uint32_t w16[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) w16[i] = i < NBR ? __float_as_uint(S[i]) : 0u;
+                ptx::tmem_st16(tl + tcol + kColS, w16);
+                if constexpr (NBR > 16) {
+                    uint32_t w8[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) w8[i] = 16 + i < NBR ? __float_as_uint(S[16 + i]) : 0u;
+                    ptx::tmem_st8(tl + tcol + kColS + 16, w8);
+                }
+            }
             float b0[K];
             bool nonsingular;
             {
@@ -883,8 +898,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                 uint32_t wv[24];
                 float rep[K];
                 coef_words<K>(b0, s_b, wv, rep);
-#pragma unroll
-                for (int a = 0; a < K; ++a) b0[a] = rep[a] * inv_sb;  // beta0 as the MMAs see it
                 coef_store(tl + tcol + kColB0, wv);
                 ptx::tmem_wait_st();
                 arrive(coefb);
@@ -965,8 +978,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             float dl[K];
             {
+                float S2[NBR];
+                {
+                    float v16[16];
+                    ptx::tmem_ld16(tl + tcol + kColS, v16);
+#pragma unroll
+                    for (int i = 0; i < 16 && i < NBR; ++i) S2[i] = v16[i];
+                    if constexpr (NBR > 16) {
+                        float v8[8];
+                        ptx::tmem_ld8(tl + tcol + kColS + 16, v8);
+#pragma unroll
+                        for (int i = 16; i < NBR; ++i) S2[i] = v8[i - 16];
+                    }
+                }
                 float Gm[K][K], Lc[K][K], dinv[K];
-                gram_from_sums<KH>(S, Gm);
+                gram_from_sums<KH>(S2, Gm);
                 cholesky<K>(Gm, Lc, dinv);
                 chol_solve<K>(Lc, dinv, cr, dl);
             }
@@ -975,6 +1001,22 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int a = 0; a < K; ++a) dc = fmaf(dl[a], cr[a], dc);
             const float sig = sqrtf(fmaxf(ss0 - dc, 0.f) / (float)(np - K));
             const bool degenerate = !(sig > kDegenerateRatio * ymax) || ymax == 0.f;
+            // beta of the centred trend: beta0 as the MMAs see it (c_hi + c_lo of its coefficient
+            // words, unscaled; read back rather than kept in registers through pass B') plus delta.
+            // The TMEM loads are warp-collective, so every lane takes them, before any branch.
+            float bt[K];
+            {
+                float wh[8], wl[8];
+                ptx::tmem_ld8(tl + tcol + kColB0, wh);
+                ptx::tmem_ld8(tl + tcol + kColB0 + kCoefLo, wl);
+#pragma unroll
+                for (int a = 0; a < K; ++a) {
+                    const uint32_t uh = __float_as_uint(wh[a >> 1]), ul = __float_as_uint(wl[a >> 1]);
+                    const float h = __half2float(__ushort_as_half((unsigned short)((a & 1) ? uh >> 16 : uh)));
+                    const float l = __half2float(__ushort_as_half((unsigned short)((a & 1) ? ul >> 16 : ul)));
+                    bt[a] = (h + l) * inv_sb + dl[a];
+                }
+            }
             // outputs known now (the rest after the monitoring scan)
             if (active) {
                 if (np <= K) {
@@ -983,10 +1025,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     write_unfitted(Q, p, BFM_PX_SINGULAR);
                 } else {
                     Q.sigma[p] = sig;
-                    // beta of the centred trend -> raw parameterisation of Eq. 2
-                    float bt[K];
-#pragma unroll
-                    for (int a = 0; a < K; ++a) bt[a] = b0[a] + dl[a];
+                    // -> raw parameterisation of Eq. 2
                     Q.beta[p] = fmaf(-bt[1], Q.c_over_s, bt[0]);
                     Q.beta[(size_t)m + p] = bt[1] * Q.inv_s;
 #pragma unroll
