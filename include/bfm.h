@@ -440,8 +440,8 @@ bfm_status bfm_serve_destroy(bfm_server_t s);
  *           so the call does not wait for earlier work in `stream`, and
  *           nothing of it refers to host memory once it returns.
  * Results equal those of bfm_monitor with BFM_ALGO_SIMT on each tile alone.
- * The first call on a device looks up the array's device address; make that
- * first call before any stream capture on the device.  Every call on a device
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and keeps it.  Every call on a device
  * shares the one array and overwrites it: two calls whose work overlaps on
  * the GPU (different streams, no ordering between them) race and give wrong
  * results -- order them on one stream or with events.

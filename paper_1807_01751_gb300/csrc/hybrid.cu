@@ -111,7 +111,6 @@ constexpr float kYScale = 4096.f, kInvYScale = 1.f / 4096.f;
 template <typename T>
 struct Dt {
     static constexpr int G = kBoxBytes / (kBoxPx * (int)sizeof(T));  // dates per stage: 8 float, 16 int16
-    static constexpr int kRow = kBoxPx;                              // elements between dates in a box
 };
 
 struct HybridParams {
@@ -438,7 +437,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     using B = Basis<KH>;
     constexpr int K = B::K, NBR = B::NBR;
     constexpr int G = Dt<T>::G;         // dates per stage
-    constexpr int SPC = 16 / G;         // stages per 16-date chunk
     extern __shared__ __align__(1024) unsigned char smem[];
     const HLayout Lo = kBatch ? Bt.lo : hyb_layout(P.n, P.npad, P.hmax);
     unsigned char* s_gh = smem + Lo.gh;
@@ -526,12 +524,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             px0 = wb * kPx;
         }
     };
-    auto params = [&](int ti) -> const HybridParams& {
-        if constexpr (kBatch)
-            return Bt.tiles[ti].P;
-        else
-            return P;
-    };
     auto dstart_of = [](int v, int n) -> int {
         const int d = v < n ? v : n;
         return d / G * G;
@@ -571,7 +563,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (ti != cur) ptx::fence_tmap_acquire(tm);  // a map in global memory
                     cur = ti;
                 }
-                const int n = params(ti).n, N = params(ti).N;
+                const HybridParams& Q = kBatch ? Bt.tiles[ti].P : P;
+                const int n = Q.n, N = Q.N;
                 const int nst_h = (n + G - 1) / G;  // stages of one history pass
                 for (int s = 0; s < nst_h && ok; ++s) ok = issue(tm, px0, s * G, keep);
                 for (int s = 0; s < nst_h && ok; ++s) ok = issue(tm, px0, s * G, drop);
@@ -637,7 +630,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 int ti;
                 int64_t px0;
                 locate(wb, ti, px0);
-                const HybridParams& Q = params(ti);
+                const HybridParams& Q = kBatch ? Bt.tiles[ti].P : P;
                 const int n = Q.n, N = Q.N;
                 const int nck = (n + 15) / 16;  // 16-date chunks of the history
                 if constexpr (kBatch) {
@@ -794,7 +787,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             int ti;
             int64_t px0;
             locate(wb, ti, px0);
-            const HybridParams& Q = params(ti);
+            const HybridParams& Q = kBatch ? Bt.tiles[ti].P : P;
             const int n = Q.n, N = Q.N, hmax = Q.hmax;
             const int nck = (n + 15) / 16;  // 16-date chunks of the history
             const int64_t m = Q.m;
@@ -1159,7 +1152,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 int ti;
                 int64_t px0;
                 locate(wb, ti, px0);
-                const HybridParams& Q = params(ti);
+                const HybridParams& Q = kBatch ? Bt.tiles[ti].P : P;
                 if (px0 + pl < Q.m) write_unfitted(Q, px0 + pl, BFM_PX_TIMEOUT);
             }
         }

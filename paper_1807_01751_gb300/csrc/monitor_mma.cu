@@ -1,36 +1,39 @@
 // Tensor-core form of the per-pixel path (int16 or float storage).
 //
-// One CTA = 128 pixels = the M of every tcgen05.mma = the 128 TMEM lanes;
-// thread m owns pixel m (TMEM lane m).  Y is streamed from global memory by
-// every thread, one date column per warp load (128 B or 64 B, coalesced),
-// eight dates ahead in registers and 32 dates ahead by L2 prefetch; the
-// history is kept in L2 (evict-last) for its second and third reads.  The
-// basis tables (fp16 hi/lo, the B operand of every MMA) sit in shared memory:
-// table A = basis rows 0..15 over all dates, table B = rows 16..31 over the
-// history.  Per tile:
+// One CTA = 128 pixels = the M of every tcgen05.mma = the 128 TMEM lanes,
+// held by 256 threads: pixel px by the pair (px, px + 128), warps w and w + 4,
+// which reach the same TMEM lane quarter.  Y arrives by TMA in [16 dates][128
+// px] blocks through a ring of S shared-memory stages (3 for float, 6 for
+// int16; full/empty mbarriers, one producer thread), with L2 hints: the
+// history is kept (evict-last) for its second read, later dates are dropped.
+// The basis tables (fp16 hi/lo, the B operand of every MMA) sit in shared
+// memory: table A = basis rows 0..15 over all dates, table B = rows 16..31
+// over the history.  Per tile:
 //
-//   normal   for 32-date chunks of the history, each thread writes three
-//            fp16 A-operand rows: the 0/1 mask and y*s_y split hi + lo
-//            (masked).  The single issuing thread runs, per 16 dates,
+//   normal   per 16-date chunk of the history each thread of a pair writes
+//            the fp16 A-operand rows of its 8-date group: the 0/1 mask and
+//            y*s_y split hi + lo (masked).  One thread issues
 //              TMEM[G] += mask x (Phi_hi + Phi_lo)       (3+6k basis sums, Eq. 6)
 //              TMEM[b] += (y_hi + y_lo) x (Phi_hi + Phi_lo)   (X'My, Eq. 6)
 //            double-buffered against the next chunk's operand writes
-//   solve    every thread: Gram from the basis sums, Cholesky, beta0 (FP32)
+//   solve    both threads of a pair: Gram from the basis sums, Cholesky,
+//            beta0 (FP32)
 //   refine   TMEM[Y] = [beta0_hi | beta0_lo] x Phi (table A read MN-major:
 //            rows = coefficients, columns = dates), 192 dates per piece;
 //            r0 = y - yhat0 on valid history dates, split hi + lo, then
 //            TMEM[c] += r0 x Phi: one refinement step beta = beta0 + G^-1 c;
 //            sum r^2 = sum r0^2 - delta'c (sigma-hat, Eq. 5)
-//   MOSUM    per 192-date piece TMEM[Y] = X beta0 + X delta; per thread, 8
-//            dates at a time: r = y - yhat, compensated prefix sums S over
-//            valid positions in a ring, windows of h valid residuals
-//            W = S_J - S_{J-h} (Eq. 3), first crossing of lambda*sqrt(log+(j/n))
-//            (Eq. 4) and the mean
+//   MOSUM    per 192-date piece TMEM[Y] = X beta0 + X delta; the first
+//            thread of a pair forms r = y - yhat 8 dates at a time and
+//            compensated prefix sums S over valid positions in a ring; the
+//            second, one group behind, the windows of h valid residuals
+//            W = S_J - S_{J-h} (Eq. 3), the first crossing of
+//            lambda*sqrt(log+(j/n)) (Eq. 4) and the mean
 //
 // Scaling: every A operand row is one pixel, so each thread scales its own
 // rows by powers of two (exact) chosen from its data, keeping fp16 hi + lo
 // splits inside fp16's range; results are scaled back exactly.  TMEM use is
-// 256 columns per CTA and shared memory about 106 KB at 414 dates, so two
+// 256 columns per CTA and shared memory about 109 KB at 414 dates, so two
 // CTAs share an SM.
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>

@@ -19,7 +19,7 @@ Named workloads:
   * ``c4``  64 uneven int16 tiles (see :func:`tiles_c4`).
 
 The critical value lambda of each workload comes from ``lambda_table.json``,
-written by ``oracle/make_lambda_table.py`` (Monte-Carlo of the limiting MOSUM
+written by ``synth/make_lambda_table.py`` (Monte-Carlo of the limiting MOSUM
 process, alpha = 0.05).
 """
 from __future__ import annotations
