@@ -236,27 +236,32 @@ __global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2)
     // the consumers' stage j kept as (slot, lap parity): slot = j % kStages, phase = (j / kStages) & 1
     int cslot = 0;
     uint32_t cphase = 0;
-    // Wait for stage j: this thread's column in it, or nullptr when the wait
-    // gave up or the CTA is aborting (warp-uniform).  A warp that gives up
-    // neither reads nor releases the stage, so the producer never refills a
-    // slot whose copy may still be in flight; it raises the abort flag at once.
+    // Wait for stage j and return this thread's column in it.  Fast path: one
+    // look at the barrier and a warp vote; the bounded wait, which also ends
+    // when another warp or the producer has raised the abort flag, runs only
+    // when some lane finds the stage not yet landed.  A warp whose wait gives up
+    // raises the abort flag and is `bad` from then on (warp-uniform): it may
+    // still read stages, whose contents no longer matter (its pixels end as
+    // TIMEOUT), but it releases none, so the producer never refills a slot whose
+    // copy may still be in flight.
     auto acquire = [&]() -> const T* {
         const int slot = cslot;
-        const bool ok = ptx::mbar_wait_bounded(full + slot, cphase, kWaitNs);
-        const bool gave_up = __any_sync(~0u, !ok);
-        if (gave_up && (threadIdx.x & 31) == 0) {
-            *abort_flag = 1u;
-            atomicOr(&g_bfm_complete_err, 1u);
-        }
-        if (gave_up || __any_sync(~0u, *abort_flag != 0u)) {
-            bad = true;
-            return nullptr;
+        bool ok = ptx::mbar_try_wait(full + slot, cphase);
+        if (!__all_sync(~0u, ok)) {
+            if (!ok) ok = wait_released(full + slot, cphase, abort_flag, kWaitNs);
+            if (__any_sync(~0u, !ok)) {
+                if ((threadIdx.x & 31) == 0 && !bad) {
+                    *abort_flag = 1u;
+                    atomicOr(&g_bfm_complete_err, 1u);
+                }
+                bad = true;
+            }
         }
         return reinterpret_cast<const T*>(stages + slot * kStageBytes) + threadIdx.x;
     };
     auto release = [&]() {  // this warp is done with stage j
         __syncwarp();
-        if ((threadIdx.x & 31) == 0) mbar_arrive(empty + cslot);
+        if ((threadIdx.x & 31) == 0 && !bad) mbar_arrive(empty + cslot);
         if (++cslot == kStages) {
             cslot = 0;
             cphase ^= 1u;
@@ -288,7 +293,6 @@ __global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2)
             uint32_t mw[G1];
             if constexpr (kStaged) {
                 const T* st = acquire();
-                if (!st) return;
 #pragma unroll
                 for (int u = 0; u < G1; ++u) raw[u] = (full || u < cnt) ? st[u * kThreads] : T(0);
             } else {
@@ -337,7 +341,6 @@ __global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2)
             T raw[G1];
             if constexpr (kStaged) {
                 const T* st = acquire();
-                if (!st) return;
 #pragma unroll
                 for (int u = 0; u < G1; ++u) raw[u] = (full || u < cnt) ? st[u * kThreads] : T(0);
             } else {
@@ -395,7 +398,6 @@ __global__ void __launch_bounds__(kStaged ? kThreads + 32 : kThreads, 2)
             if constexpr (kStaged) {
                 (void)old;
                 const T* st = acquire();
-                if (!st) return;
 #pragma unroll
                 for (int u = 0; u < G3; ++u) raw[u] = (full || u < cnt) ? st[u * kThreads] : T(0);
             } else {

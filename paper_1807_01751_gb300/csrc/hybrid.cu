@@ -736,9 +736,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         const bool test_mode = P.wait_ns < 1000u;
         auto acquire = [&]() -> const T* {
             const int slot = cslot;
-            bool ok = test_mode ? ptx::mbar_test_wait(full + slot, cphase) : ptx::mbar_try_wait(full + slot, cphase);
+            bool ok = !test_mode && ptx::mbar_try_wait(full + slot, cphase);
             if (!__all_sync(~0u, ok)) {
-                if (!ok && !test_mode) ok = wait_bar(full + slot, cphase, abort_flag, P.wait_ns);
+                if (!ok)
+                    ok = test_mode ? ptx::mbar_test_wait(full + slot, cphase)
+                                   : wait_bar(full + slot, cphase, abort_flag, P.wait_ns);
                 if (__any_sync(~0u, !ok)) {
                     if (lane == 0) raise_abort(abort_flag);
                     bad = true;

@@ -204,29 +204,35 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
     // the consumers' stage j kept as (slot, lap parity): slot = j % kStages, phase = (j / kStages) & 1
     int cslot = 0;
     uint32_t cphase = 0;
-    // Wait for stage j: this thread's column in it, or nullptr when the wait
-    // gave up or the CTA is aborting (warp-uniform).  A warp that gives up
-    // neither reads nor releases the stage, so the producer never refills a
-    // slot whose copy may still be in flight; it raises the abort flag at once.
+    // Wait for stage j and return this thread's column in it.  Fast path: one
+    // look at the barrier and a warp vote.  The bounded wait, which also ends
+    // when another warp or the producer has raised the abort flag, runs only
+    // when some lane finds the stage not yet landed; a bound below 1 us (a test
+    // of the failure path) makes the first look a non-blocking one and the only
+    // one.  A warp whose wait gives up raises the abort flag and is `bad` from
+    // then on (warp-uniform): it may still read stages, whose contents no longer
+    // matter (its pixels end as TIMEOUT), but it releases none, so the producer
+    // never refills a slot whose copy may still be in flight.
+    const bool test_mode = P.wait_ns < 1000u;
     auto acquire = [&]() -> const T* {
         const int slot = cslot;
-        // a bound below 1 us (a test of the failure path): one look at the barrier
-        const bool ok = P.wait_ns < 1000u ? ptx::mbar_test_wait(full + slot, cphase)
-                                          : ptx::mbar_wait_bounded(full + slot, cphase, P.wait_ns);
-        const bool gave_up = __any_sync(~0u, !ok);
-        if (gave_up && (threadIdx.x & 31) == 0) {
-            *abort_flag = 1u;
-            atomicOr(&g_bfm_stream_err, 1u);
-        }
-        if (gave_up || __any_sync(~0u, *abort_flag != 0u)) {
-            bad = true;
-            return nullptr;
+        bool ok = !test_mode && ptx::mbar_try_wait(full + slot, cphase);
+        if (!__all_sync(~0u, ok)) {
+            if (!ok) ok = test_mode ? ptx::mbar_test_wait(full + slot, cphase)
+                                    : wait_released(full + slot, cphase, abort_flag, P.wait_ns);
+            if (__any_sync(~0u, !ok)) {
+                if ((threadIdx.x & 31) == 0 && !bad) {
+                    *abort_flag = 1u;
+                    atomicOr(&g_bfm_stream_err, 1u);
+                }
+                bad = true;
+            }
         }
         return reinterpret_cast<const T*>(stages + slot * kStageBytes) + threadIdx.x;
     };
     auto release = [&]() {  // this warp is done with stage j
         __syncwarp();
-        if ((threadIdx.x & 31) == 0) mbar_arrive(empty + cslot);
+        if ((threadIdx.x & 31) == 0 && !bad) mbar_arrive(empty + cslot);
         if (++cslot == kStages) {
             cslot = 0;
             cphase ^= 1u;
@@ -272,7 +278,6 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
             constexpr bool full = decltype(full_c)::value;
             const int cnt = full ? G : n - d0;
             const T* st = acquire();
-            if (!st) return;
 #pragma unroll
             for (int u = 0; u < G; ++u) {
                 float y;
@@ -308,7 +313,6 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
             constexpr bool full = decltype(full_c)::value;
             const int cnt = full ? G : n - d0;
             const T* st = acquire();
-            if (!st) return;
 #pragma unroll
             for (int u = 0; u < G; ++u) {
                 float y;
@@ -357,7 +361,6 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
             constexpr bool full = decltype(full_c)::value;
             const int cnt = full ? G : n - d0;
             const T* st = acquire();
-            if (!st) return;
             if (__any_sync(~0u, q + G > 0)) {  // some pixel of the warp may reach its window in this batch
 #pragma unroll
                 for (int u = 0; u < G; ++u) {
@@ -391,7 +394,6 @@ __global__ void __launch_bounds__(kThreads + 32, 2)
             constexpr bool full = decltype(full_c)::value;
             const int cnt = full ? G : N - d0;
             const T* st = acquire();
-            if (!st) return;
             // boundary test W^2 inv_scale^2 - b^2 > 0 (MO^2 > b^2): its maximum over
             // the batch, the first crossing searched only in a batch that has one
             float cv[G], blk = 0.f, cmax = -INFINITY;
