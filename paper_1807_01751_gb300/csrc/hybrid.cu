@@ -729,10 +729,15 @@ __global__ void __launch_bounds__(kThreads, 1)
         int cslot = 0;
         uint32_t cphase = 0;
         uint32_t cc = 0, pc = 0, accpar = 0, cdpar = 0, dpar = 0;
-        // Wait for the next stage: this thread's column in it, or nullptr (warp-uniform)
-        // when the wait gave up or the CTA is aborting; a warp that gives up neither
-        // reads nor releases the stage.  Fast path: one look at the barrier.  A bound
-        // below 1 us (a test of the failure path) makes every look non-blocking.
+        // Wait for the next stage and return this thread's column in it.  Fast path:
+        // one look at the barrier and a warp vote; the bounded wait (which also ends
+        // on the abort flag) only when some lane finds the stage not yet landed.  A
+        // bound below 1 us (a test of the failure path) makes that look a
+        // non-blocking one and the only one.  A warp whose wait gives up raises the
+        // abort flag and is `bad` from then on (warp-uniform): it may finish reading
+        // the chunk it is in, whose contents no longer matter (its pixels end as
+        // TIMEOUT), but it releases no stage, so the producer never refills a slot
+        // whose copy may still be in flight.
         const bool test_mode = P.wait_ns < 1000u;
         auto acquire = [&]() -> const T* {
             const int slot = cslot;
@@ -744,14 +749,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (__any_sync(~0u, !ok)) {
                     if (lane == 0) raise_abort(abort_flag);
                     bad = true;
-                    return nullptr;
                 }
             }
             return sbase + slot * (kStageBytes / (int)sizeof(T));
         };
         auto release = [&]() {
             __syncwarp();
-            if (lane == 0) mbar_arrive(empty + cslot);
+            if (lane == 0 && !bad) mbar_arrive(empty + cslot);
             const int ns = cslot + 1;
             cphase ^= ns == kStages ? 1u : 0u;
             cslot = ns == kStages ? 0 : ns;
@@ -811,7 +815,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int d8 = 16 * c + 8 * h;
                     if (d8 < n) {  // warp-uniform: the dates exist
                         if (h == 0 || G == 8) stg = acquire();
-                        if (!stg) break;
                         const T* st = stg + (G == 16 ? h * 8 * kBoxPx : 0);
                         if (d8 + 8 <= n)
                             pass_a8<true>(ob, st, d8, n, yv + 8 * h, mk + 4 * h, ymax);
@@ -924,7 +927,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int d8 = 16 * c + 8 * h;
                     if (d8 < n) {
                         if (h == 0 || G == 8) stg = acquire();
-                        if (!stg) break;
                         const T* st = stg + (G == 16 ? h * 8 * kBoxPx : 0);
                         const bool scan = __any_sync(~0u, rem < 8);  // a pixel may reach its window start
                         const bool fullb = d8 + 8 <= n;
@@ -1075,7 +1077,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ptx::tc_fence_after();
                 if (off % G == 0) {
                     stg = acquire();
-                    if (!stg) break;
                 }
                 const T* st = stg + (off % G);  // dates of the stage are rows of kBoxPx elements
                 const T* st8 = stg + (off % G) * kBoxPx;
