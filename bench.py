@@ -39,7 +39,7 @@ METRIC = "BFAST-monitor pixels/s at 8.4M px x 414 dates; p50/p99 tile latency"
 # DRAM bytes per pixel per launch from the ncu captures summarised in
 # profiles/ (None once the kernel changes after the capture).
 TRAFFIC_PER_PX = {"f32": (1.7866e9 / 1048576,), "f32simt": (1.784346e9 / 1048576,), "f32stream": (None,),
-                  "i16": (None,), "f32hybrid": (2.063879e9 / 1048576,), "i16hybrid": (None,),
+                  "i16": (None,), "f32hybrid": (1.836045e9 / 1048576,), "i16hybrid": (None,),
                   "i16stream": (None,), "f32complete": (None,)}
 SAMPLE_PX = 4096  # pixels of each timed form checked against the oracle (outside the timed region)
 
