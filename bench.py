@@ -168,15 +168,25 @@ def cpu_oracle_one_core(Y_host, dates, n_hist, h_frac, lam):
 
 
 def cpu_oracle_c1():
-    """The oracle on all host cores on the c1 scene (4096 pixels x 228 dates)."""
+    """The oracle on the c1 scene (4096 pixels x 228 dates): on all host cores,
+    and on one core (OMP_NUM_THREADS=1 in a child process)."""
     import oracle
     import synth
     w1 = synth.workload("c1")
     t0 = time.perf_counter()
     oracle.monitor(w1["dates"], w1["Y"], k=3, f=23.0, n_hist=w1["n_hist"], h_frac=w1["h_frac"], lam=w1["lam"])
     dt = time.perf_counter() - t0
+    code = ("import sys, time; sys.path.insert(0, %r); import oracle, synth; w = synth.workload('c1'); "
+            "t0 = time.perf_counter(); oracle.monitor(w['dates'], w['Y'], k=3, f=23.0, n_hist=w['n_hist'], "
+            "h_frac=w['h_frac'], lam=w['lam']); print(w['m'] / (time.perf_counter() - t0))" % ROOT)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                       env=dict(os.environ, OMP_NUM_THREADS="1"), timeout=600)
+    try:
+        one = float(r.stdout.strip().splitlines()[-1])
+    except (ValueError, IndexError):
+        one = None
     return {"value": w1["m"] / dt, "unit": "pixels/s", "cores": int(os.environ.get("OMP_NUM_THREADS", os.cpu_count())),
-            "workload": "c1: 4096 pixels x 228 dates, n_hist 100, K 8, 30 % i.i.d. missing"}
+            "one_core": one, "workload": "c1: 4096 pixels x 228 dates, n_hist 100, K 8, 30 % i.i.d. missing"}
 
 
 def oracle_on(Y, dates, n_hist, h_frac, lam):
