@@ -493,7 +493,9 @@ template <int KH, typename T, bool kMask, bool kStaged>
 bfm_status launch_variant(const CUtensorMap& tm, const CompleteParams& P, int grid, size_t smem, cudaStream_t st) {
     auto* fn = complete_kernel<KH, T, kMask, kStaged>;
     if (smem > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // the opt-in maximum, not this launch's size: launches of other sizes (other
+        // scenes, other host threads) never find a smaller limit in place
+        const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e != cudaSuccess) return cuda_fail(e, "bfm_monitor (complete): shared memory attribute");
     }
     fn<<<grid, kStaged ? kThreads + 32 : kThreads, smem, st>>>(tm, P);

@@ -1171,7 +1171,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 template <int KH, typename T, bool kMask>
 bfm_status launch_one(const CUtensorMap& tm, const HybridParams& P, int grid, size_t smem, cudaStream_t st) {
     auto* fn = hybrid_kernel<KH, T, kMask, false>;
-    const cudaError_t ea = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the opt-in maximum, not this launch's size: launches of other sizes (other
+    // scenes, other host threads) never find a smaller limit in place
+    const cudaError_t ea = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
     if (ea != cudaSuccess) return cuda_fail(ea, "bfm_monitor (hybrid): shared memory attribute");
     fn<<<grid, kThreads, smem, st>>>(tm, P, HybBatch{});
     const cudaError_t e = cudaGetLastError();
@@ -1432,7 +1434,8 @@ bfm_status hyb_group_node(HybGroup* g, cudaGraph_t graph, const cudaGraphNode_t*
     bt.blocks = g->blocks;
     bt.lo = hyb_layout(g->nmax, g->npadmax, g->hmaxmax);
     const size_t smem = bt.lo.total;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the opt-in maximum: other groups of the same variant may need more than this one
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap);
     if (e != cudaSuccess) return cuda_fail(e, "bfm_batch: hybrid kernel shared memory attribute");
     // the single-tile parameters are unused but for the stage-wait bound
     static CUtensorMap tm_unused;  // zero; never read by the batched kernel

@@ -484,7 +484,9 @@ template <int KH, typename T, bool kMask>
 bfm_status launch_one(const CUtensorMap& tm, const StreamParams& P, int grid, size_t smem, cudaStream_t st) {
     auto* fn = stream_kernel<KH, T, kMask>;
     if (smem > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        // the opt-in maximum, not this launch's size: launches of other sizes (other
+        // scenes, other host threads) never find a smaller limit in place
+        const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         if (e != cudaSuccess) return cuda_fail(e, "bfm_monitor (stream): shared memory attribute");
     }
     fn<<<grid, kThreads + 32, smem, st>>>(tm, P);
