@@ -131,6 +131,35 @@ def test_batch_hybrid_variants(bfm):
     b.close()
 
 
+def test_batch_hybrid_groups_of_one_variant(bfm):
+    """Two float k = 3 tiles whose shared-memory layouts fit one SM alone but
+    not together (226.5 KB and 217.3 KB; 236.7 KB as one layout): the batch
+    runs them as two hybrid groups of the same kernel variant with different
+    shared-memory sizes, in one graph, and both reproduce single calls bit for
+    bit."""
+    b = bfm.Batch()
+    outs, singles = [], []
+    for i, (N, n_hist) in enumerate(((414, 228), (600, 200))):
+        d_, Y, _ = synth.scene(seed=40 + i, m=2048, N=N, n_hist=n_hist, f=23.0, k_gen=3, intercept=0.5, slope=0.0,
+                               coef_umax=0.3, noise_sd=0.04, miss="markov", p_a=0.25, p_b=0.375, break_frac=0.15,
+                               step=(-0.5, -0.1), dtype="f32")
+        d = bfm.Design(d_, 3, 23.0)
+        Yd = torch.from_numpy(Y).cuda()
+        lam = synth.lambda_for_horizon(N / n_hist)
+        outs.append(b.add(d, Yd, n_hist=n_hist, h_frac=0.25, lam=lam))
+        assert b.form(i) == bfm.BFM_ALGO_HYBRID
+        singles.append(bfm.monitor(d, Yd, n_hist=n_hist, h_frac=0.25, lam=lam, algo=bfm.BFM_ALGO_HYBRID))
+    b.run()
+    b.run()
+    torch.cuda.synchronize()
+    assert bfm.bfm_device_errors() == 0
+    for i, (o, sgl) in enumerate(zip(outs, singles)):
+        a, c = to_numpy(o), to_numpy(sgl)
+        for key in a:
+            np.testing.assert_array_equal(a[key].view(np.uint8), c[key].view(np.uint8), err_msg=f"tile {i} {key}")
+    b.close()
+
+
 def test_batch_forms_api(bfm):
     """bfm_batch_set_forms takes AUTO, HYBRID, MMA or SIMT before the first
     tile only; bfm_batch_tile_form answers -1 for an unknown id."""
