@@ -66,11 +66,12 @@ enum {
 
 /* Algorithm variants for bfm_monitor_ex.  BFM_ALGO_AUTO takes the hybrid
  * form (BFM_ALGO_HYBRID, below) where it applies, else the streaming form
- * (BFM_ALGO_STREAM) where it applies, else the tensor-core form where it applies -- its shared memory (basis tables over
- * the N dates, a MOSUM ring of floor(h_frac * n_hist) + 17 prefix sums per
- * pixel, the Y stages) fits one SM, and Y can be described by a tensor map
- * (16-byte aligned base, m >= 128, rows a multiple of 16 bytes) -- else the
- * CUDA-core form (bfm_algo_auto tells which).
+ * (BFM_ALGO_STREAM) where it applies, else the tensor-core form where it
+ * applies -- its shared memory (basis tables over the N dates, a MOSUM ring
+ * of floor(h_frac * n_hist) + 17 prefix sums per pixel, the Y stages) fits
+ * one SM, and Y can be described by a tensor map (16-byte aligned base,
+ * m >= 128, rows a multiple of 16 bytes) -- else the CUDA-core form
+ * (bfm_algo_auto tells which).
  * BFM_ALGO_COMPLETE is never chosen by AUTO: it is the fast path for series
  * without missing values (Section 3, Eq. 8-11), where every pixel shares the
  * history design X_h and beta = M y_h with one M = (X_h'X_h)^-1 X_h' built in
@@ -265,8 +266,9 @@ bfm_status bfm_trace(bfm_design_t d, const void *Y, int dtype, const uint32_t *m
                      float *resid, void *stream);
 
 /* The form BFM_ALGO_AUTO takes for these arguments (BFM_ALGO_HYBRID,
- * BFM_ALGO_STREAM, BFM_ALGO_MMA or BFM_ALGO_SIMT; no work, no device access).  Y and m matter only through
- * Y's alignment and m; a NULL or invalid design gives BFM_ALGO_SIMT. */
+ * BFM_ALGO_STREAM, BFM_ALGO_MMA or BFM_ALGO_SIMT; no work, no device
+ * access).  Y and m matter only through Y's alignment and m; a NULL or
+ * invalid design gives BFM_ALGO_SIMT. */
 int bfm_algo_auto(bfm_design_t d, int dtype, int n_hist, double h_frac, const void *Y, int64_t m);
 
 /* As bfm_monitor with an explicit algorithm (bfm_algo).  BFM_ALGO_MMA needs
