@@ -301,9 +301,9 @@ bfm_status bfm_monitor_host(bfm_design_t d, const void *Y_host, int dtype, const
  * series lengths (their own designs), harmonics and storage types processed
  * by one CUDA-graph replay of persistent kernels: one per hybrid kernel
  * variant (k, storage, mask) and shared-memory layout for the tiles the
- * hybrid form takes (512-pixel blocks, taken in a fixed order), one per
- * tensor-core kernel variant for the tiles the tensor-core form takes
- * (128-pixel blocks from a work counter), and one CUDA-core kernel for the
+ * hybrid form takes (512-pixel blocks, taken in a fixed order), one
+ * kernel node per tile the tensor-core form takes (the kernel of a single
+ * call, over the tile's 128-pixel blocks), and one CUDA-core kernel for the
  * rest (32-pixel blocks); bfm_batch_form and bfm_batch_tile_form tell which.  The paper processes one scene per
  * call (Algorithm 2); batching is a serving extension with the same
  * per-pixel results: every pixel's outputs equal those of bfm_monitor_ex
@@ -316,12 +316,11 @@ bfm_status bfm_monitor_host(bfm_design_t d, const void *Y_host, int dtype, const
  *                       receives its index.  The batch holds a reference to
  *                       the design.
  *   bfm_batch_run       enqueues the whole batch on `stream`: a graph of the
- *                       work-counter resets, the hybrid kernels (one CTA per
- *                       SM) and the tensor-core kernels (up to 2 CTAs per SM),
- *                       a chain, and the CUDA-core kernel (CTAs = SM count x
- *                       CTAs per SM, taking `grab` 32-pixel blocks at a time;
- *                       after the chain when the batch has hybrid tiles, else
- *                       a parallel branch).  The first run after adds uploads the tile
+ *                       work-counter reset, the hybrid kernels (one CTA per
+ *                       SM; a chain), then in parallel branches the
+ *                       tensor-core tile nodes and the CUDA-core kernel
+ *                       (CTAs = SM count x CTAs per SM, taking `grab`
+ *                       32-pixel blocks at a time).  The first run after adds uploads the tile
  *                       table and instantiates the graph; later runs replay it.
  *   bfm_batch_autotune  times every (CTAs per SM, grab in {1,2,4,8})
  *                       candidate on this batch (3 replays each, CUDA events on

@@ -6,16 +6,15 @@
 // by kernel variant (k, storage, mask) and a shared-memory layout that holds
 // the group's largest tables and ring; per group one persistent kernel (one
 // CTA per SM) takes 512-pixel blocks in a fixed order and finds the owning
-// tile by binary search (hybrid.cu).  Tensor-core tiles are grouped by kernel
-// variant; per variant a persistent grid (up to 2 CTAs per SM) takes 128-pixel
-// blocks from a device counter and finds the owning tile the same way.  The
-// CUDA-core tiles go to one persistent kernel whose CTAs take 32-pixel blocks,
-// `grab` at a time.  The counter resets (one memset node), the hybrid and
-// tensor-core kernels (a chain) and the CUDA-core kernel (after the chain
-// when there are hybrid tiles, else a parallel branch) form one graph,
-// instantiated once and replayed.  An autotuner times (CTAs per SM, grab) for
-// the CUDA-core kernel on the batch itself and caches the best pair per batch
-// signature.
+// tile by binary search (hybrid.cu).  Each tensor-core tile is one kernel node,
+// the kernel a single call launches over the tile's own 128-pixel blocks.  The
+// CUDA-core tiles go to one persistent kernel whose CTAs take 32-pixel blocks
+// from a device counter, `grab` at a time.  The counter reset (one memset
+// node), the hybrid kernels (a chain after it) and, after them in parallel
+// branches, the tensor-core tile nodes and the CUDA-core kernel form one
+// graph, instantiated once and replayed.  An autotuner times (CTAs per SM,
+// grab) for the CUDA-core kernel on the batch itself and caches the best pair
+// per batch signature.
 #include <cuda.h>
 
 #include <algorithm>
@@ -46,11 +45,8 @@ struct bfm_batch_s {
     std::vector<CUtensorMap> tmaps;
     int64_t total_blocks = 0;
     size_t smem = 0;
-    // tensor-core tiles, per group = kernel variant x (2 CTAs per SM or 1)
-    static constexpr int kGroups = 24;
-    std::vector<bfm::MmaBatchTile> mtiles[kGroups];
-    int64_t mblocks[kGroups] = {};
-    size_t msmem[kGroups] = {};
+    // tensor-core tiles: one kernel node each (arguments and dynamic shared memory)
+    std::vector<std::pair<bfm::MmaBatchTile, size_t>> mtiles;
     // hybrid tiles, per group = kernel variant x shared-memory layout
     std::vector<bfm::HybGroup*> hgroups;
     int ntiles_all = 0;
@@ -60,8 +56,7 @@ struct bfm_batch_s {
     // device copies
     void* d_tiles = nullptr;
     void* d_tmaps = nullptr;
-    void* d_mtiles = nullptr;               // all variants, concatenated
-    unsigned long long* d_counter = nullptr;  // [0] CUDA-core kernel, [1 + g] tensor-core group g
+    unsigned long long* d_counter = nullptr;  // the CUDA-core kernel's work counter
     bool dirty = true;
     // launch configuration
     int ctas_per_sm = 0;  // 0 = not tuned yet (use the occupancy maximum)
@@ -101,17 +96,14 @@ void free_dev(bfm_batch_s* b) {
     b->graph = nullptr;
     if (b->d_tiles) cudaFree(b->d_tiles);
     if (b->d_tmaps) cudaFree(b->d_tmaps);
-    if (b->d_mtiles) cudaFree(b->d_mtiles);
     if (b->d_counter) cudaFree(b->d_counter);
-    b->d_tiles = b->d_tmaps = b->d_mtiles = nullptr;
+    b->d_tiles = b->d_tmaps = nullptr;
     b->d_counter = nullptr;
 }
 
 bfm_status upload(bfm_batch_s* b) {
     if (!b->dirty) return BFM_OK;
     free_dev(b);
-    size_t nm = 0;
-    for (int v = 0; v < bfm_batch_s::kGroups; ++v) nm += b->mtiles[v].size();
     cudaError_t e = cudaSuccess;
     for (auto* g : b->hgroups) {
         const bfm_status st = hyb_group_upload(g);
@@ -119,19 +111,11 @@ bfm_status upload(bfm_batch_s* b) {
     }
     if (!b->tiles.empty()) e = cudaMalloc(&b->d_tiles, sizeof(BatchTileDesc) * b->tiles.size());
     if (e == cudaSuccess && !b->tmaps.empty()) e = cudaMalloc(&b->d_tmaps, sizeof(CUtensorMap) * b->tmaps.size());
-    if (e == cudaSuccess && nm) e = cudaMalloc(&b->d_mtiles, sizeof(MmaBatchTile) * nm);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, (1 + bfm_batch_s::kGroups) * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, sizeof(unsigned long long));
     if (e == cudaSuccess && !b->tiles.empty())
         e = cudaMemcpy(b->d_tiles, b->tiles.data(), sizeof(BatchTileDesc) * b->tiles.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !b->tmaps.empty())
         e = cudaMemcpy(b->d_tmaps, b->tmaps.data(), sizeof(CUtensorMap) * b->tmaps.size(), cudaMemcpyHostToDevice);
-    size_t off = 0;
-    for (int v = 0; v < bfm_batch_s::kGroups && e == cudaSuccess; ++v) {
-        if (b->mtiles[v].empty()) continue;
-        e = cudaMemcpy(static_cast<MmaBatchTile*>(b->d_mtiles) + off, b->mtiles[v].data(),
-                       sizeof(MmaBatchTile) * b->mtiles[v].size(), cudaMemcpyHostToDevice);
-        off += b->mtiles[v].size();
-    }
     if (e != cudaSuccess) return cuda_fail(e, "bfm_batch: uploading tile descriptors");
     b->dirty = false;
     return BFM_OK;
@@ -163,13 +147,14 @@ bfm_status build_graph(bfm_batch_s* b, int grid, int grab) {
     mp.dst = b->d_counter;
     mp.value = 0;
     mp.elementSize = 4;
-    mp.width = 2 * (1 + bfm_batch_s::kGroups);  // the counters
+    mp.width = 2;  // the CUDA-core kernel's 64-bit work counter
     mp.height = 1;
     mp.pitch = 0;
     e = cudaGraphAddMemsetNode(&memset_node, b->graph, nullptr, 0, &mp);
     if (e != cudaSuccess) return cuda_fail(e, "bfm_batch: memset node");
     bfm_status st = BFM_OK;
-    // hybrid groups, then the tensor-core groups: a chain after the memset
+    // the hybrid groups: a chain after the memset (their CTAs take work blocks in a fixed
+    // order and so should find every SM free)
     cudaGraphNode_t prev = memset_node;
     for (auto* g : b->hgroups) {
         cudaGraphNode_t node;
@@ -177,23 +162,16 @@ bfm_status build_graph(bfm_batch_s* b, int grid, int grab) {
         if (st != BFM_OK) return st;
         prev = node;
     }
-    size_t off = 0;
-    for (int v = 0; v < bfm_batch_s::kGroups; ++v) {
-        if (b->mtiles[v].empty()) continue;
+    // after them, in parallel branches: one node per tensor-core tile (the kernel a single
+    // call launches, over the tile's own blocks) and the persistent CUDA-core kernel
+    for (auto& mt : b->mtiles) {
         cudaGraphNode_t node;
-        const int mgrid = sm_count(b->device) * mma_ctas_per_sm(b->msmem[v]);
-        st = mma_batch_node(v / 2, static_cast<const MmaBatchTile*>(b->d_mtiles) + off, (int)b->mtiles[v].size(),
-                            b->mblocks[v], b->d_counter + 1 + v, mgrid, b->msmem[v], b->graph, &prev, &node);
+        st = mma_tile_node(mt.first, mt.second, b->graph, &prev, &node);
         if (st != BFM_OK) return st;
-        prev = node;
-        off += b->mtiles[v].size();
     }
-    // CUDA-core tiles: a parallel branch beside the tensor-core kernels, or after the hybrid
-    // kernels, whose CTAs take their work blocks in a fixed order and so should find every SM free
     if (!b->tiles.empty() && b->total_blocks > 0) {
-        const cudaGraphNode_t dep = b->hgroups.empty() ? memset_node : prev;
         st = batch_launch_kernel(b->d_tiles, b->d_tmaps, (int)b->tiles.size(), b->total_blocks, b->d_counter, grab,
-                                 grid, b->smem, nullptr, b->graph, &dep, &kernel_node);
+                                 grid, b->smem, nullptr, b->graph, &prev, &kernel_node);
         if (st != BFM_OK) return st;
     }
     e = cudaGraphInstantiate(&b->exec, b->graph, 0);
@@ -304,12 +282,7 @@ bfm_status bfm_batch_add(bfm_batch_t b, bfm_design_t d, const void* Y, int dtype
         if (!mma_fill_tile(d, dtype, Y, mask_bits, m, n_hist, h_frac, lambda, break_idx, mean_mosum, sigma, beta,
                            status, &mt, &msm))
             return BFM_EUNSUPPORTED;
-        // group: kernel variant, and whether two CTAs of this tile share an SM
-        const int v = 2 * mma_variant(d->k, dtype, mask_bits != nullptr) + (mma_ctas_per_sm(msm) == 2 ? 0 : 1);
-        mt.block0 = b->mblocks[v];
-        b->mtiles[v].push_back(mt);
-        b->mblocks[v] += (m + 127) / 128;
-        b->msmem[v] = std::max(b->msmem[v], msm);
+        b->mtiles.emplace_back(mt, msm);
         return hold(BFM_ALGO_MMA);
     }
     int br = 0, nb = 0;

@@ -97,12 +97,10 @@ struct MmaParams {
     float* maxmo;  // nullable: MO of largest magnitude per pixel
 };
 
-// One tile of a batched tensor-core launch (device-side; the tensor map
-// first, so that it sits on a 64-byte boundary in the device table).
+// One tile of a batched tensor-core launch: the arguments of its kernel node.
 struct MmaBatchTile {
     CUtensorMap tm;  // 64-byte aligned type
     MmaParams P;
-    int64_t block0;  // first 128-pixel work block of this tile
     int kh, dtype, has_mask;
 };
 
@@ -113,13 +111,10 @@ bool mma_fill_tile(const bfm_design_s* d, int dtype, const void* Y, const uint32
                    uint8_t* status, MmaBatchTile* out, size_t* smem);
 // Kernel variant (0..11) of a tile: harmonics k, storage type, explicit mask.
 int mma_variant(int k, int dtype, bool has_mask);
-// Add the persistent tensor-core batch kernel of one variant (its tiles only,
-// block0 numbered within the variant) to `graph` after `dep` (nullable).
-bfm_status mma_batch_node(int variant, const MmaBatchTile* d_tiles, int ntiles, int64_t total_blocks,
-                          unsigned long long* counter, int grid, size_t smem, cudaGraph_t graph,
-                          const cudaGraphNode_t* dep, cudaGraphNode_t* node_out);
-// CTAs of the tensor-core kernel that share one SM at this shared memory (1 or 2).
-int mma_ctas_per_sm(size_t smem);
+// Add the single-tile tensor-core kernel of tile t (its own grid of 128-pixel
+// blocks, as bfm_monitor launches it) to `graph` after `dep` (nullable).
+bfm_status mma_tile_node(const MmaBatchTile& t, size_t smem, cudaGraph_t graph, const cudaGraphNode_t* dep,
+                         cudaGraphNode_t* node_out);
 
 // Each kernel translation unit keeps its own device error word (bit 0: a
 // tile-load wait gave up); these read and clear it, synchronising `s`.

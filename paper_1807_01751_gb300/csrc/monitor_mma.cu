@@ -821,44 +821,6 @@ __global__ void __launch_bounds__(kThreads, 2) mma_kernel(const __grid_constant_
     if ((threadIdx.x >> 5) == 0) ptx::tmem_dealloc(tmem, kTmemCols);
 }
 
-// Persistent form over a batch of tiles of one (k, storage, mask) variant:
-// CTAs take 128-pixel blocks from a device counter, find the owning tile by
-// binary search over the tiles' first-block numbers and run mma_block with
-// its parameters and tensor map.
-template <int KH, typename T, bool kMask>
-__global__ void __launch_bounds__(kThreads, 2) mma_batch_kernel(const MmaBatchTile* __restrict__ tiles, int ntiles,
-                                                                int64_t total_blocks,
-                                                                unsigned long long* counter) {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem);
-    long long* s_blk = reinterpret_cast<long long*>(smem + 8);
-    if ((threadIdx.x >> 5) == 0) ptx::tmem_alloc(tslot, kTmemCols);
-    ptx::tc_fence_before();
-    __syncthreads();
-    ptx::tc_fence_after();
-    const uint32_t tmem = *tslot;
-    while (true) {
-        if (threadIdx.x == 0) *s_blk = (long long)atomicAdd(counter, 1ull);
-        __syncthreads();
-        const int64_t blk = *s_blk;
-        __syncthreads();  // read by all before thread 0 takes the next one
-        if (blk >= total_blocks) break;
-        int lo = 0, hi = ntiles - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (tiles[mid].block0 <= blk) lo = mid;
-            else hi = mid - 1;
-        }
-        const MmaBatchTile* t = tiles + lo;
-        // the two threads that issue TMA loads (history passes, MOSUM pass)
-        if (threadIdx.x == 0 || threadIdx.x == kTile) ptx::fence_tmap_acquire(&t->tm);
-        mma_block<KH, T, kMask>(&t->tm, t->P, blk - t->block0, smem, tmem);
-    }
-    ptx::tc_fence_before();
-    __syncthreads();
-    if ((threadIdx.x >> 5) == 0) ptx::tmem_dealloc(tmem, kTmemCols);
-}
-
 // Ring of prefix sums: the h slots behind the oldest position of the group
 // the second thread reads, that group and the one the first thread writes.
 int ring_len(int n_hist, double h_frac) {
@@ -1040,47 +1002,40 @@ bool mma_fill_tile(const bfm_design_s* d, int dtype, const void* Y, const uint32
     return true;
 }
 
-int mma_ctas_per_sm(size_t smem) { return smem + 1024 <= 114 * 1024 ? 2 : 1; }
-
 namespace {
 template <int KH, typename T, bool kMask>
-void* batch_kernel_fn() {
-    return (void*)mma_batch_kernel<KH, T, kMask>;
+void* tile_kernel_fn() {
+    return (void*)mma_kernel<KH, T, kMask>;
 }
 }  // namespace
 
 int mma_variant(int k, int dtype, bool has_mask) { return ((k - 1) * 2 + (dtype == BFM_I16 ? 1 : 0)) * 2 + (has_mask ? 1 : 0); }
 
-bfm_status mma_batch_node(int variant, const MmaBatchTile* d_tiles, int ntiles, int64_t total_blocks,
-                          unsigned long long* counter, int grid, size_t smem, cudaGraph_t graph,
-                          const cudaGraphNode_t* dep, cudaGraphNode_t* node_out) {
+bfm_status mma_tile_node(const MmaBatchTile& t, size_t smem, cudaGraph_t graph, const cudaGraphNode_t* dep,
+                         cudaGraphNode_t* node_out) {
     static void* const fns[12] = {
-        batch_kernel_fn<1, float, false>(),   batch_kernel_fn<1, float, true>(),
-        batch_kernel_fn<1, int16_t, false>(), batch_kernel_fn<1, int16_t, true>(),
-        batch_kernel_fn<2, float, false>(),   batch_kernel_fn<2, float, true>(),
-        batch_kernel_fn<2, int16_t, false>(), batch_kernel_fn<2, int16_t, true>(),
-        batch_kernel_fn<3, float, false>(),   batch_kernel_fn<3, float, true>(),
-        batch_kernel_fn<3, int16_t, false>(), batch_kernel_fn<3, int16_t, true>()};
+        tile_kernel_fn<1, float, false>(),   tile_kernel_fn<1, float, true>(),
+        tile_kernel_fn<1, int16_t, false>(), tile_kernel_fn<1, int16_t, true>(),
+        tile_kernel_fn<2, float, false>(),   tile_kernel_fn<2, float, true>(),
+        tile_kernel_fn<2, int16_t, false>(), tile_kernel_fn<2, int16_t, true>(),
+        tile_kernel_fn<3, float, false>(),   tile_kernel_fn<3, float, true>(),
+        tile_kernel_fn<3, int16_t, false>(), tile_kernel_fn<3, int16_t, true>()};
+    const int variant = mma_variant(t.kh, t.dtype, t.has_mask != 0);
     if (variant < 0 || variant >= 12) {
         set_error("bfm_batch: bad tensor-core variant");
         return BFM_EINVAL;
     }
-    static thread_local int configured[12] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (configured[variant] != dev) {
-        cudaError_t e = cudaFuncSetAttribute(fns[variant], cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(mma_batch_kernel)");
-        configured[variant] = dev;
-    }
-    void* args[] = {(void*)&d_tiles, (void*)&ntiles, (void*)&total_blocks, (void*)&counter};
+    cudaError_t e = cudaFuncSetAttribute(fns[variant], cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(mma_kernel)");
+    // the arguments are copied into the node: the tile's tensor map and parameters
+    void* args[] = {(void*)&t.tm, (void*)&t.P};
     cudaKernelNodeParams kp{};
     kp.func = fns[variant];
-    kp.gridDim = dim3((unsigned)grid);
+    kp.gridDim = dim3((unsigned)((t.P.m + kTile - 1) / kTile));
     kp.blockDim = dim3(kThreads);
     kp.sharedMemBytes = (unsigned)smem;
     kp.kernelParams = args;
-    const cudaError_t e = cudaGraphAddKernelNode(node_out, graph, dep, dep ? 1 : 0, &kp);
+    e = cudaGraphAddKernelNode(node_out, graph, dep, dep ? 1 : 0, &kp);
     if (e != cudaSuccess) return cuda_fail(e, "bfm_batch: tensor-core kernel node");
     return BFM_OK;
 }

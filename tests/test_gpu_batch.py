@@ -71,8 +71,8 @@ def _mask_bits(rng, N, m, p_keep=0.85):
 
 def test_batch_tensor_core_variants(bfm):
     """Tiles of every harmonic order in both storage types, widths rounded to
-    multiples of 8, in a batch limited to the tensor-core form: the persistent
-    tensor-core kernels (one per variant) reproduce single calls bit for bit."""
+    multiples of 8, in a batch limited to the tensor-core form: the tile nodes
+    of the graph reproduce single calls bit for bit, on two replays."""
     tiles = _tiles(scale=0.02, count=16, px_multiple=8)
     b = bfm.Batch(forms=bfm.BFM_ALGO_MMA)
     outs, singles, forms = [], [], set()
