@@ -8,7 +8,11 @@ Markov cloud gaps; 10 % of pixels with a level shift.  One step = one
 bfm_monitor call over the whole scene (every step of the per-pixel path).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--form f32|i16] [--no-e2e] [--no-cpu-baseline]
+                  [--forms f32hybrid,f32stream,...] [--pixels M] [--no-e2e]
+                  [--no-cpu-baseline] [--no-c4c5]
+
+The first of --forms (default: the hybrid form on float32) is the headline
+line; the others are timed beside it under "forms".
 
 Prints ONE JSON line (rank 0).  Under torchrun (N > 1) every rank processes
 its own full scene (weak scaling, no collective on the data path); value is
